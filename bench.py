@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark: Kob-Andersen binary LJ, N = 32 000, rho = 1.2, one GB300.
+
+Workload (the 32k configuration): lattice + 0.05 jitter start at T = 2.0,
+2000 Nose-Hoover steps to T = 0.8 (set-up, untimed), then NVE at dt = 0.005
+with a cell + Verlet list of skin 0.3 (rebuilt on the device when any
+particle has moved more than skin/2).
+
+One bench step = one persistent launch that advances the system 100 MD steps
+(force + velocity Verlet + reductions + every list rebuild the dynamics
+triggers), i.e. one md_step_nve(dt, 100) call. --steps K timed steps follow
+--warmup W untimed ones; the default K = 100 covers the configuration's
+10 000 NVE steps. L2 is flushed (a 256 MB write) between timed steps.
+
+value     = atom-steps/s of the mixed-precision path, device-timed (CUDA
+            events on the system's stream), inputs resident in HBM.
+e2e       = the same metric through the public C ABI with host buffers:
+            md_set_state(host) + md_step_nve(100, thermo log to host) +
+            md_get_state(host) per step.
+fp64      = the all-FP64 GPU path on the same protocol, with its drift.
+roofline  = FP32 issue bound ("alu") of the persistent kernel: algorithmic
+            FLOPs per launch / launch time against 2*128*SMs*f_max.
+cpu_baseline = the FP64 oracle (plain C, all pairs, one core) on a bounded
+            sample (a few MD steps of the same system).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s and pair-evals/s (mixed vs FP64 GPU) at equal NVE energy drift"
+UNIT = "atom-steps/s"
+N = 32000
+SEED = 2
+T_START, T_NVT = 2.0, 0.8
+NVT_STEPS = 2000
+CHUNK = 100
+LOG_EVERY = 10
+# counting convention for the pair loop (per list entry)
+FLOP_PAIR_IN = 26   # interacting entry: dr 3, r^2 5, rcp 1, r^-6 2, sigma^6 r^-6 1, force 4, accumulate 6, energy 4
+FLOP_PAIR_OUT = 8   # rejected entry: dr 3, r^2 5 (fixed-point minimum image is integer arithmetic)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="kamd_clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([float(r[1]) for r in rows])
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def drift_per_tau(log, dt):
+    """Least-squares slope of E_tot/N against time (energy per particle per tau)."""
+    e = log["etot_per_n"][:, 0]
+    t = log["step"][:, 0] * dt
+    if len(e) < 3:
+        return None, None
+    A = np.vstack([t, np.ones_like(t)]).T
+    coef, *_ = np.linalg.lstsq(A, e, rcond=None)
+    return float(coef[0]), float(np.std(e - A @ coef))
+
+
+def setup_system(kamd, wl, prec, device):
+    L = wl.box_length(N)
+    types = wl.ka_types(N, SEED)
+    s = kamd.System(N, L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
+    s.init_lattice(T_START, 0.05, SEED)
+    s.step_nvt(wl.DT, NVT_STEPS, T_NVT, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
+    return s, L, types
+
+
+def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.step_nve(dt, CHUNK)
+    logs, times = [], []
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        logs.append(s.step_nve(dt, CHUNK, log_every=log_every))
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    times = [ev0[k].elapsed_time(ev1[k]) * 1e-3 for k in range(steps)]
+    log = np.concatenate(logs, axis=0)
+    return np.array(times), log
+
+
+def run_e2e(torch, kamd, s, dt, steps):
+    """Public API with host buffers: set_state(host) + step (log to host) + get_state(host)."""
+    pos, vel, _ = s.get_state()
+    pos = np.ascontiguousarray(pos)
+    vel = np.ascontiguousarray(vel)
+    img = np.zeros((s.n_total, 3), dtype=np.int32)
+    nlog = CHUNK // LOG_EVERY
+    log = np.zeros(nlog, dtype=kamd.THERMO_DTYPE)
+    h = s.handle
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        kamd.md_set_state(h, pos, vel)
+        kamd.md_step_nve(h, dt, CHUNK, log, LOG_EVERY)
+        kamd.md_get_state(h, pos, vel, img, 0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    h2d = 2 * 3 * 8 * s.n_total
+    d2h = (2 * 3 * 8 + 3 * 4) * s.n_total + log.nbytes
+    return el, h2d, d2h
+
+
+def cpu_baseline(wl, seconds_target=15.0):
+    """The oracle as it stands (one core, all pairs) on a few MD steps of the same system."""
+    import oracle
+    L = wl.box_length(N)
+    types = wl.ka_types(N, SEED).astype(np.int32)
+    params = oracle.Params(wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS)
+    pos, vel = oracle.init_lattice(N, L, T_START, SEED)
+    t0 = time.perf_counter()
+    f, _, _ = oracle.forces(pos, types, params, L)
+    t_force = time.perf_counter() - t0
+    nsteps = max(1, min(10, int(seconds_target / max(t_force, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    oracle.run(pos, vel, types, params, L, wl.DT, nsteps, forces_in=f, log_every=0)
+    el = time.perf_counter() - t0
+    return {"value": N * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} velocity-Verlet steps of the N=32000 system (all-pairs FP64 C oracle, 1 thread)"}
+
+
+def reference_arm(args, rank, world):
+    import torch.distributed as dist  # noqa: F401
+    from paper_2001_07089_gb300 import workloads as wl
+    if rank != 0:
+        return
+    import oracle
+    L = wl.box_length(N)
+    types = wl.ka_types(N, SEED).astype(np.int32)
+    params = oracle.Params(wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS)
+    pos, vel = oracle.init_lattice(N, L, T_START, SEED)
+    f, _, _ = oracle.forces(pos, types, params, L)
+    st = {"pos": pos, "vel": vel, "forces": f}
+    for _ in range(args.warmup):
+        st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
+    el = time.perf_counter() - t0
+    v = N * args.steps / el
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": "ka32k: KA 80:20 N=32000 rho=1.2, NVE dt=0.005; one bench step = one "
+                                             "oracle MD step (all pairs)"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"{args.steps} all-pairs velocity-Verlet steps of N=32000, 1 thread"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kamd", choices=["kamd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2001_07089_gb300 import kamd
+    from paper_2001_07089_gb300 import workloads as wl
+    kamd.load()
+    dev = torch.cuda.current_device()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # ---- mixed-precision path (the measured value); every rank runs its own replica
+    s, L, types = setup_system(kamd, wl, "mixed", dev)
+    tuning = s.tuning
+    if not args.no_autotune:
+        tuning, _ = s.autotune(wl.DT, probe_steps=200)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    total = float(times.sum())
+    if dist:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    info = s.info()
+    pairs = s.count_pairs()
+    entries = info["list_entries"]
+    drift_mixed, fluct_mixed = drift_per_tau(log, wl.DT)
+    value = world * N * CHUNK * args.steps / total
+    pair_evals = entries * CHUNK * args.steps * world / total
+    flop_step = FLOP_PAIR_IN * 2 * pairs + FLOP_PAIR_OUT * (entries - 2 * pairs)
+    launch_s = total / args.steps
+    achieved = flop_step * CHUNK / launch_s / 1e12
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 2 * FP32_LANES_PER_SM * nsm * SM_MAX_MHZ * 1e6 / 1e12
+    e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, max(3, min(args.steps, 20)))
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_value = world * N * CHUNK * e2e_steps / e2e_el
+    s.close()
+
+    # ---- all-FP64 GPU path on the same protocol (context for the mixed number)
+    fp64 = None
+    if rank == 0:
+        k64 = args.fp64_steps if args.fp64_steps is not None else max(3, min(args.steps, 20))
+        s64, _, _ = setup_system(kamd, wl, "fp64", dev)
+        if not args.no_autotune:
+            s64.autotune(wl.DT, probe_steps=50)
+        t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush)
+        d64, f64 = drift_per_tau(log64, wl.DT)
+        fp64 = {"value": N * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
+                "drift_per_particle_per_tau": d64, "etot_fluct_per_particle": f64,
+                "tuning": s64.tuning}
+        s64.close()
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(wl)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ka32k: Kob-Andersen 80:20, N=32000, rho=1.2, L=29.876, lattice+0.05 jitter at "
+                               "T=2.0, 2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + "
+                               "Verlet list skin 0.3 rebuilt on device; one bench step = 100 MD steps",
+                   "n": N, "md_steps_per_bench_step": CHUNK, "timed_md_steps": CHUNK * args.steps,
+                   "precision": "mixed: 64-bit fixed-point positions, FP32 velocities/forces/pair math, "
+                                "FP64 reductions",
+                   "l2": "flushed between timed steps (256 MB write)", "tuning": tuning,
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "pair_evals_per_s": pair_evals,
+        "useful_pair_evals_per_s": 2 * pairs * CHUNK * args.steps * world / total,
+        "list_entries": entries, "pairs_within_cutoff": pairs,
+        "drift_per_particle_per_tau": drift_mixed, "etot_fluct_per_particle": fluct_mixed,
+        "fp64": fp64,
+        "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "md_persistent<mixed> (one launch = 100 MD steps)",
+                     "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,1209 @@
+// md_api.cu -- the C ABI declared in include/kamd.h: system set-up, device
+// memory, state transfer, and the launches of the persistent step kernel.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kamd.h"
+#include "md_device.cuh"
+#include "md_internal.cuh"
+
+struct md_system {
+  // configuration
+  int nrep = 0, ntypes = 0;
+  int64_t n_total = 0;  // particles, caller order
+  int64_t ntot = 0;     // slots (padded)
+  int ntiles = 0;
+  bool mixed = true;
+  std::vector<int64_t> n_per, out0;
+  std::vector<double> L_per;
+  double eps[16] = {0}, sig[16] = {0}, rc[16] = {0};
+  double mass = 1.0;
+  md_tuning tun{4, 256, 0.3};
+  cudaStream_t stream = nullptr;
+  int device = 0, nsm = 0;
+  int grid = 0;
+  int maxrows = 0;
+  int64_t ncells = 0;
+  bool have_state = false;
+  // host mirrors
+  std::vector<RepDev> reps;
+  CtlDev ctl{};
+  // device memory
+  RepDev* d_reps = nullptr;
+  int32_t* d_tile_rep = nullptr;
+  CtlDev* d_ctl = nullptr;
+  uint64_t* d_pfx = nullptr;
+  uint4* d_pq[2] = {nullptr, nullptr};
+  float* d_velf = nullptr;
+  float* d_frcf = nullptr;
+  uint4* d_xbq = nullptr;
+  double4_32a* d_p4[2] = {nullptr, nullptr};
+  double* d_veld = nullptr;
+  double* d_frcd = nullptr;
+  double4_32a* d_xbd = nullptr;
+  int32_t* d_gid = nullptr;
+  uint8_t* d_typ = nullptr;
+  int32_t* d_img = nullptr;
+  uint64_t* d_tpfx = nullptr;
+  double4_32a* d_tp4 = nullptr;
+  void* d_tvel = nullptr;
+  void* d_tfrc = nullptr;
+  int32_t* d_tgid = nullptr;
+  uint8_t* d_ttyp = nullptr;
+  int32_t* d_timg = nullptr;
+  int32_t* d_cellof = nullptr;
+  int32_t* d_ccount = nullptr;
+  int32_t* d_cstart = nullptr;
+  int32_t* d_ccursor = nullptr;
+  int32_t* d_scat = nullptr;
+  int32_t* d_nbr = nullptr;
+  int32_t* d_nnb = nullptr;
+  double* d_part[2] = {nullptr, nullptr};
+  uint8_t* d_typ_caller = nullptr;
+  int32_t* d_rep_of_caller = nullptr;
+  double* d_msd_ref = nullptr;
+  ThermoDev* d_thermo = nullptr;
+  int64_t thermo_cap = 0;
+  double* d_io = nullptr;  // caller-order staging (n_total*3 doubles)
+  int32_t* d_io_i = nullptr;
+  unsigned long long* d_rdf = nullptr;
+  int64_t rdf_nbins = 0;
+  double rdf_dr = 0.0;
+  int64_t rdf_meas = 0;
+  double* d_msd_part = nullptr;
+  unsigned long long* d_count = nullptr;
+  size_t bytes = 0;
+  size_t list_bytes = 0;
+  unsigned long long timeout_ns = 10ull * 1000 * 1000 * 1000;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+md_status fail(md_system* s, md_status code, const std::string& msg) {
+  if (s) s->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+md_status cuda_fail(md_system* s, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(s, e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA, m);
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+  } while (0)
+
+template <typename T>
+md_status dalloc(md_system* s, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaMalloc");
+  s->bytes += count * sizeof(T);
+  e = cudaMemsetAsync(*p, 0, count * sizeof(T), s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemsetAsync");
+  return MD_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+#define CKS(call)                 \
+  do {                            \
+    md_status st_ = (call);       \
+    if (st_ != MD_OK) return st_; \
+  } while (0)
+
+// ------------------------------------------------------------------ kernels
+
+// Map caller-order particle g to its slot: identity order inside a replica.
+__global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const RepDev* reps, const int32_t* rep_of,
+                            const uint8_t* typ_caller, const double* pos, const double* vel, int cur, uint64_t* pfx,
+                            uint4* pq, float* velf, float* frcf, uint4* xbq, double4_32a* p4, double* veld,
+                            double* frcd, double4_32a* xbd, int32_t* gid, uint8_t* typ, int32_t* img, int32_t* nnb) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_total) return;
+  const RepDev& R = reps[rep_of[g]];
+  const int64_t i = R.off + (g - R.out0);
+  const uint32_t t = typ_caller[g];
+  double x[3];
+  for (int c = 0; c < 3; ++c) x[c] = kamd::wrap_box(pos[3 * g + c], R.L);
+  if (mixed) {
+    uint32_t hi[3];
+    for (int c = 0; c < 3; ++c) {
+      const uint64_t u = kamd::to_fixed(x[c], R.invL);
+      pfx[c * ntot + i] = u;
+      hi[c] = (uint32_t)(u >> 32);
+      velf[c * ntot + i] = vel ? (float)vel[3 * g + c] : 0.0f;
+      frcf[c * ntot + i] = 0.0f;
+    }
+    pq[i] = make_uint4(hi[0], hi[1], hi[2], t);
+    xbq[i] = pq[i];
+  } else {
+    p4[i] = make_double4_32a(x[0], x[1], x[2], (double)t);
+    xbd[i] = p4[i];
+    for (int c = 0; c < 3; ++c) {
+      veld[c * ntot + i] = vel ? vel[3 * g + c] : 0.0;
+      frcd[c * ntot + i] = 0.0;
+    }
+  }
+  for (int c = 0; c < 3; ++c) img[c * ntot + i] = 0;
+  gid[i] = (int32_t)g;
+  typ[i] = (uint8_t)t;
+  nnb[i] = 0;
+}
+
+// Simple-cubic lattice with jitter (Sec. "Initialization of positions").
+__global__ void k_lattice(int64_t n_total, const RepDev* reps, const int32_t* rep_of, double jitter, uint64_t seed,
+                          double* pos) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_total) return;
+  const RepDev& R = reps[rep_of[g]];
+  const int64_t p = g - R.out0, n = R.n;
+  int64_t m = 1;
+  while (m * m * m < n) ++m;
+  const double a = R.L / (double)m;
+  const int64_t sites = m * m * m;
+  const int64_t site = (int64_t)(((unsigned __int128)p * (unsigned __int128)sites) / (unsigned __int128)n);
+  const int64_t k[3] = {site % m, (site / m) % m, site / (m * m)};
+  double u[3];
+  kamd::jitter3(seed, (uint32_t)p, u);
+  for (int c = 0; c < 3; ++c) {
+    double x = (0.5 + (double)k[c]) * a + jitter * u[c];
+    if (x >= R.L) x -= R.L;
+    else if (x < 0.0) x += R.L;
+    pos[3 * g + c] = x;
+  }
+}
+
+__global__ void k_get_state(bool mixed, int64_t ntot, const RepDev* reps, const int32_t* tile_rep, int cur,
+                            const uint64_t* pfx, const float* velf, const double4_32a* p4, const double* veld,
+                            const int32_t* gid, const int32_t* img, double* pos, double* vel, int32_t* imgo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const RepDev& R = reps[tile_rep[i >> 5]];
+  if (i - R.off >= R.n) return;
+  const int64_t g = gid[i];
+  for (int c = 0; c < 3; ++c) {
+    if (pos) pos[3 * g + c] = mixed ? kamd::from_fixed(pfx[c * ntot + i], R.L) : (c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z);
+    if (vel) vel[3 * g + c] = mixed ? (double)velf[c * ntot + i] : veld[c * ntot + i];
+    if (imgo) imgo[3 * g + c] = img[c * ntot + i];
+  }
+}
+
+__global__ void k_get_forces(bool mixed, int64_t ntot, const RepDev* reps, const int32_t* tile_rep, const float* frcf,
+                             const double* frcd, const int32_t* gid, double* f) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const RepDev& R = reps[tile_rep[i >> 5]];
+  if (i - R.off >= R.n) return;
+  const int64_t g = gid[i];
+  for (int c = 0; c < 3; ++c) f[3 * g + c] = mixed ? (double)frcf[c * ntot + i] : frcd[c * ntot + i];
+}
+
+__global__ void k_set_images(int64_t n_total, int64_t ntot, const RepDev* reps, const int32_t* rep_of,
+                             const int32_t* imgs, int32_t* img) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_total) return;
+  const RepDev& R = reps[rep_of[g]];
+  const int64_t i = R.off + (g - R.out0);
+  for (int c = 0; c < 3; ++c) img[c * ntot + i] = imgs[3 * g + c];
+}
+
+// Unwrapped caller-order positions x + L*image (MSD reference / current).
+__global__ void k_unwrapped(bool mixed, int64_t ntot, const RepDev* reps, const int32_t* tile_rep, const uint64_t* pfx,
+                            const double4_32a* p4, const int32_t* gid, const int32_t* img, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const RepDev& R = reps[tile_rep[i >> 5]];
+  if (i - R.off >= R.n) return;
+  const int64_t g = gid[i];
+  for (int c = 0; c < 3; ++c) {
+    const double x = mixed ? kamd::from_fixed(pfx[c * ntot + i], R.L) : (c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z);
+    out[3 * g + c] = x + R.L * (double)img[c * ntot + i];
+  }
+}
+
+// Per-tile sums of squared displacement per type (Eq. (msdwithi)); counts in
+// the second half of the partial row.
+__global__ void k_msd_tiles(bool mixed, int ntiles, int ntypes, int64_t ntot, const RepDev* reps, const int32_t* tile_rep,
+                            const uint64_t* pfx, const double4_32a* p4, const int32_t* gid, const uint8_t* typ,
+                            const int32_t* img, const double* ref, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (tile >= ntiles) return;
+  const RepDev& R = reps[tile_rep[tile]];
+  const int64_t i = tile * 32 + lane;
+  double d2 = 0.0;
+  int t = -1;
+  if (i - R.off < R.n) {
+    const int64_t g = gid[i];
+    t = typ[i];
+    for (int c = 0; c < 3; ++c) {
+      const double x = mixed ? kamd::from_fixed(pfx[c * ntot + i], R.L) : (c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z);
+      const double d = x + R.L * (double)img[c * ntot + i] - ref[3 * g + c];
+      d2 += d * d;
+    }
+  }
+  for (int a = 0; a < ntypes; ++a) {
+    const double v = kamd::warp_sum(t == a ? d2 : 0.0);
+    const double cnt = kamd::warp_sum(t == a ? 1.0 : 0.0);
+    if (lane == 0) {
+      part[tile * MD_NPART + a] = v;
+      part[tile * MD_NPART + MD_MAXTYPES + a] = cnt;
+    }
+  }
+}
+
+// One thread per type: fixed-order sum over all tiles.
+__global__ void k_msd_final(int ntiles, int ntypes, const double* part, double* out) {
+  const int a = threadIdx.x;
+  if (a >= ntypes) return;
+  double s = 0.0, c = 0.0;
+  for (int t = 0; t < ntiles; ++t) {
+    s += part[(int64_t)t * MD_NPART + a];
+    c += part[(int64_t)t * MD_NPART + MD_MAXTYPES + a];
+  }
+  out[a] = c > 0 ? s / c : 0.0;
+}
+
+// Pair-distance histogram of Sec. "Radial distribution function with
+// Python": every unordered pair with r < nbins*dr adds 2 (like) or 1 (unlike)
+// to bin floor(r/dr) of its replica (integer counts; exact, order-free).
+__global__ void k_rdf(bool mixed, int64_t ntot, int nbins, double dr, double skin, const RepDev* reps,
+                      const int32_t* tile_rep, int cur, const uint4* pq, const uint64_t* pfx, const double4_32a* p4,
+                      const uint8_t* typ, const int32_t* cstart, unsigned long long* hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const int r = tile_rep[i >> 5];
+  const RepDev& R = reps[r];
+  if (i - R.off >= R.n) return;
+  const double rmax = dr * nbins, rmax2 = rmax * rmax;
+  const int ti = typ[i];
+  double xi[3];
+  uint64_t ui[3];
+  for (int c = 0; c < 3; ++c) {
+    if (mixed) ui[c] = pfx[c * ntot + i];
+    else xi[c] = c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z;
+  }
+  const int nc = R.nc;
+  const int layers = nc > 0 ? (int)ceil((rmax + skin) * (1.0 + 1e-6) / (double)R.cellw) : 0;
+  const bool all = nc == 0 || 2 * layers + 1 > nc;
+  int cx = 0, cy = 0, cz = 0;
+  if (!all) {
+    if (mixed) {
+      cx = (int)(((uint64_t)(uint32_t)(ui[0] >> 32) * (uint64_t)nc) >> 32);
+      cy = (int)(((uint64_t)(uint32_t)(ui[1] >> 32) * (uint64_t)nc) >> 32);
+      cz = (int)(((uint64_t)(uint32_t)(ui[2] >> 32) * (uint64_t)nc) >> 32);
+    } else {
+      const double sc = (double)nc * R.invL;
+      cx = min(max((int)(xi[0] * sc), 0), nc - 1);
+      cy = min(max((int)(xi[1] * sc), 0), nc - 1);
+      cz = min(max((int)(xi[2] * sc), 0), nc - 1);
+    }
+  }
+  unsigned long long* h = hist + (int64_t)r * 3 * nbins;
+  auto visit = [&](int64_t j) {
+    if (j <= i) return;
+    double d[3];
+    for (int c = 0; c < 3; ++c) {
+      if (mixed) {
+        d[c] = (double)(int64_t)(ui[c] - pfx[c * ntot + j]) * (R.L * (1.0 / 18446744073709551616.0));
+      } else {
+        const double xj = c == 0 ? p4[j].x : c == 1 ? p4[j].y : p4[j].z;
+        double e = xi[c] - xj;
+        if (e > 0.5 * R.L) e -= R.L;
+        else if (e < -0.5 * R.L) e += R.L;
+        d[c] = e;
+      }
+    }
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < rmax2)) return;
+    const int k = (int)(sqrt(r2) / dr);
+    if (k >= nbins) return;
+    const int tj = typ[j];
+    if (ti == 0 && tj == 0) atomicAdd(&h[k], 2ull);
+    else if (ti == 1 && tj == 1) atomicAdd(&h[nbins + k], 2ull);
+    else atomicAdd(&h[2 * nbins + k], 1ull);
+  };
+  if (all) {
+    for (int64_t j = R.off; j < R.off + R.n; ++j) visit(j);
+  } else {
+    // cells are those of the last list build; every particle has moved less
+    // than half a skin since, so layers computed with rmax + skin cover all pairs
+    for (int oz = -layers; oz <= layers; ++oz)
+      for (int oy = -layers; oy <= layers; ++oy)
+        for (int ox = -layers; ox <= layers; ++ox) {
+          const int c = (((cz + oz + 8 * nc) % nc) * nc + (cy + oy + 8 * nc) % nc) * nc + (cx + ox + 8 * nc) % nc;
+          const int lo = cstart[R.cs0 + c], hi = cstart[R.cs0 + c + 1];
+          for (int j = lo; j < hi; ++j) visit(j);
+        }
+  }
+}
+
+// Pairs inside their cutoff, counted from the full Verlet list (each pair twice).
+__global__ void k_count_pairs(bool mixed, int64_t ntot, int T, int maxrows, int ntypes, const RepDev* reps,
+                              const int32_t* tile_rep, int cur, const uint4* pq, const double4_32a* p4, const int32_t* nbr,
+                              const int32_t* nnb, const float* rc2f, const double* rc2d, unsigned long long* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const RepDev& R = reps[tile_rep[i >> 5]];
+  if (i - R.off >= R.n) return;
+  const int gsz = 32 * T;
+  const int32_t* lb = nbr + (i >> 5) * (int64_t)maxrows * gsz + (i & 31) * T;
+  unsigned long long c = 0;
+  const int cnt = nnb[i];
+  for (int k = 0; k < cnt; ++k) {
+    const int j = lb[(k / T) * gsz + (k % T)];
+    if (mixed) {
+      const uint4 a = pq[i], b = pq[j];
+      const float dx = (float)(int)(a.x - b.x) * R.fxs, dy = (float)(int)(a.y - b.y) * R.fxs,
+                  dz = (float)(int)(a.z - b.z) * R.fxs;
+      c += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rc2f[a.w * ntypes + b.w];
+    } else {
+      const double4_32a a = p4[i], b = p4[j];
+      double d[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
+      for (int q = 0; q < 3; ++q) {
+        if (d[q] > 0.5 * R.L) d[q] -= R.L;
+        else if (d[q] < -0.5 * R.L) d[q] += R.L;
+      }
+      c += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2d[(int)a.w * ntypes + (int)b.w];
+    }
+  }
+  if (c) atomicAdd(out, c);
+}
+
+int blocks_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+// ------------------------------------------------------------------ host helpers
+
+md_status upload_reps(md_system* s) {
+  CK(cudaMemcpyAsync(s->d_reps, s->reps.data(), sizeof(RepDev) * s->nrep, cudaMemcpyHostToDevice, s->stream));
+  return MD_OK;
+}
+md_status download_reps(md_system* s) {
+  CK(cudaMemcpyAsync(s->reps.data(), s->d_reps, sizeof(RepDev) * s->nrep, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MD_OK;
+}
+md_status upload_ctl(md_system* s) {
+  CK(cudaMemcpyAsync(s->d_ctl, &s->ctl, sizeof(CtlDev), cudaMemcpyHostToDevice, s->stream));
+  return MD_OK;
+}
+md_status download_ctl(md_system* s) {
+  CK(cudaMemcpyAsync(&s->ctl, s->d_ctl, sizeof(CtlDev), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MD_OK;
+}
+
+double rc_max(const md_system* s) {
+  double m = 0;
+  for (int t = 0; t < s->ntypes * s->ntypes; ++t) m = std::max(m, s->rc[t]);
+  return m;
+}
+
+// Cells per edge and list capacity follow from the skin; both are recomputed
+// whenever the tuning changes.
+void layout_cells(md_system* s) {
+  const double rl = rc_max(s) + s->tun.skin;
+  int64_t cell0 = 0;
+  for (int r = 0; r < s->nrep; ++r) {
+    RepDev& R = s->reps[r];
+    int nc = (int)std::floor(R.L / rl);
+    if (nc < 3) nc = 0;
+    if (nc > 1024) nc = 1024;
+    R.nc = nc;
+    R.cellw = nc > 0 ? (float)(R.L / nc) : 0.0f;
+    R.cell0 = cell0;
+    R.cs0 = cell0 + r;
+    cell0 += (int64_t)nc * nc * nc;
+  }
+  s->ncells = cell0;
+}
+
+int list_capacity(const md_system* s) {
+  const double rl = rc_max(s) + s->tun.skin;
+  double dens = 0;
+  int64_t nmax = 0;
+  for (int r = 0; r < s->nrep; ++r) {
+    dens = std::max(dens, (double)s->n_per[r] / (s->L_per[r] * s->L_per[r] * s->L_per[r]));
+    nmax = std::max(nmax, s->n_per[r]);
+  }
+  double est = 4.0 / 3.0 * M_PI * rl * rl * rl * dens;
+  int cap = (int)std::ceil(1.5 * est + 32);
+  if (cap > nmax - 1) cap = (int)std::max<int64_t>(nmax - 1, 1);
+  return cap;
+}
+
+md_status alloc_cells_and_list(md_system* s, int cap_entries) {
+  const int T = s->tun.threads_per_atom;
+  dfree(s->d_ccount);
+  dfree(s->d_cstart);
+  dfree(s->d_ccursor);
+  dfree(s->d_nbr);
+  s->maxrows = (cap_entries + T - 1) / T;
+  CKS(dalloc(s, &s->d_ccount, (size_t)s->ncells));
+  CKS(dalloc(s, &s->d_cstart, (size_t)(s->ncells + s->nrep)));
+  CKS(dalloc(s, &s->d_ccursor, (size_t)s->ncells));
+  const size_t entries = (size_t)s->ntiles * s->maxrows * 32 * T;
+  CKS(dalloc(s, &s->d_nbr, entries));
+  s->list_bytes = entries * 4;
+  return MD_OK;
+}
+
+md_status mark_rebuild_all(md_system* s) {
+  CKS(download_reps(s));
+  for (auto& R : s->reps) R.want_rebuild = 1;
+  CKS(upload_reps(s));
+  CKS(download_ctl(s));
+  s->ctl.pending |= MD_FLAG_REBUILD;
+  return upload_ctl(s);
+}
+
+md_status configure_grid(md_system* s) {
+  const int b = s->tun.block_size;
+  int per_sm = 0;
+  CK(md_occupancy(s->mixed, b, &per_sm));
+  if (per_sm < 1) return fail(s, MD_ERR_INVALID_ARG, "block size too large for the persistent kernel");
+  s->grid = per_sm * s->nsm;
+  return MD_OK;
+}
+
+void fill_tables(const md_system* s, KParams& p) {
+  const int nt = s->ntypes;
+  for (int t = 0; t < nt * nt; ++t) {
+    const double e = s->eps[t], sg = s->sig[t], rc = s->rc[t];
+    const double sr6 = std::pow(sg / rc, 6.0);
+    const double vc = 4.0 * e * (sr6 * sr6 - sr6);
+    const double rl = rc + s->tun.skin;
+    p.tab_d[t][0] = rc * rc;
+    p.tab_d[t][1] = sg * sg;
+    p.tab_d[t][2] = 48.0 * e;
+    p.tab_d[t][3] = 4.0 * e;
+    p.vsh_d[t] = vc;
+    p.rl2_d[t] = rl * rl;
+    for (int k = 0; k < 4; ++k) p.tab_f[t][k] = (float)p.tab_d[t][k];
+    p.vsh_f[t] = (float)vc;
+    p.rl2_f[t] = (float)(rl * rl);
+  }
+}
+
+KParams make_params(const md_system* s) {
+  KParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nrep = s->nrep;
+  p.ntypes = s->ntypes;
+  p.ntot = s->ntot;
+  p.ntiles = s->ntiles;
+  p.T = s->tun.threads_per_atom;
+  p.maxrows = s->maxrows;
+  fill_tables(s, p);
+  p.mass = s->mass;
+  p.inv_mass = 1.0 / s->mass;
+  p.skin_half2 = 0.25 * s->tun.skin * s->tun.skin;
+  p.timeout_ns = s->timeout_ns;
+  p.reps = s->d_reps;
+  p.tile_rep = s->d_tile_rep;
+  p.ctl = s->d_ctl;
+  p.pfx = s->d_pfx;
+  p.pq[0] = s->d_pq[0];
+  p.pq[1] = s->d_pq[1];
+  p.velf = s->d_velf;
+  p.frcf = s->d_frcf;
+  p.xbq = s->d_xbq;
+  p.p4[0] = s->d_p4[0];
+  p.p4[1] = s->d_p4[1];
+  p.veld = s->d_veld;
+  p.frcd = s->d_frcd;
+  p.xbd = s->d_xbd;
+  p.gid = s->d_gid;
+  p.typ = s->d_typ;
+  p.img = s->d_img;
+  p.t_pfx = s->d_tpfx;
+  p.t_p4 = s->d_tp4;
+  p.t_vel = s->d_tvel;
+  p.t_frc = s->d_tfrc;
+  p.t_gid = s->d_tgid;
+  p.t_typ = s->d_ttyp;
+  p.t_img = s->d_timg;
+  p.cellof = s->d_cellof;
+  p.ccount = s->d_ccount;
+  p.cstart = s->d_cstart;
+  p.ccursor = s->d_ccursor;
+  p.scat = s->d_scat;
+  p.nbr = s->d_nbr;
+  p.nnb = s->d_nnb;
+  p.part[0] = s->d_part[0];
+  p.part[1] = s->d_part[1];
+  return p;
+}
+
+// Run the persistent kernel for one operation, growing the neighbour list
+// and relaunching when it overflows. *steps_out receives completed steps.
+md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int64_t nstep_boltz, uint64_t seed,
+                 int64_t log_every, int64_t log_cap, int64_t* steps_out) {
+  int64_t done = 0;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    // clear the barrier counter and any error flag of an earlier launch
+    CKS(download_ctl(s));
+    s->ctl.bar_count = 0;
+    s->ctl.pending &= MD_FLAG_REBUILD;
+    s->ctl.err_where = 0;
+    CKS(upload_ctl(s));
+    KParams p = make_params(s);
+    p.op = op;
+    p.kind = kind;
+    p.dt = dt;
+    p.nsteps = nsteps - done;
+    p.nstep_boltz = nstep_boltz;
+    p.seed = seed;
+    p.log_every = log_every;
+    p.log_step0 = done;
+    p.log_cap = log_cap;
+    p.thermo = s->d_thermo;
+    CK(md_launch_persistent(s->mixed, p, s->grid, s->tun.block_size, s->stream));
+    CKS(download_ctl(s));
+    if (op == MD_OP_STEPS) done += s->ctl.steps_done;
+    const int pend = s->ctl.pending;
+    if (pend & MD_FLAG_TIMEOUT) {
+      s->have_state = false;
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "grid barrier timed out (phase %d); state is undefined, call md_set_state",
+                    s->ctl.err_where);
+      return fail(s, MD_ERR_TIMEOUT, buf);
+    }
+    if (pend & MD_FLAG_UNSTABLE) {
+      if (steps_out) *steps_out = done;
+      return fail(s, MD_ERR_UNSTABLE, "NaN/Inf state or a particle moved >= L/4 in one step");
+    }
+    if (pend & MD_FLAG_OVERFLOW) {
+      const int cap = s->maxrows * s->tun.threads_per_atom;
+      CKS(alloc_cells_and_list(s, cap + cap / 2 + 16));
+      CKS(mark_rebuild_all(s));
+      continue;
+    }
+    if (steps_out) *steps_out = done;
+    return MD_OK;
+  }
+  return fail(s, MD_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing after growing it 8 times");
+}
+
+md_status ensure_thermo(md_system* s, int64_t records) {
+  if (records <= s->thermo_cap) return MD_OK;
+  dfree(s->d_thermo);
+  CKS(dalloc(s, &s->d_thermo, (size_t)records));
+  s->thermo_cap = records;
+  return MD_OK;
+}
+
+md_status reset_msd_ref(md_system* s) {
+  const int b = 256;
+  k_unwrapped<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, s->d_reps, s->d_tile_rep, s->d_pfx,
+                                                           s->d_p4[s->ctl.cur], s->d_gid, s->d_img, s->d_msd_ref);
+  CK(cudaGetLastError());
+  return MD_OK;
+}
+
+md_status after_new_state(md_system* s) {
+  s->ctl = CtlDev{};
+  s->ctl.pending = MD_FLAG_REBUILD;
+  s->ctl.cur = 0;
+  s->ctl.step = 0;
+  CKS(download_reps(s));
+  for (auto& R : s->reps) {
+    R.want_rebuild = 1;
+    R.xi = R.g = R.lns = R.lns_next = R.xi_a = 0.0;
+  }
+  CKS(upload_reps(s));
+  CKS(upload_ctl(s));
+  s->have_state = true;
+  CKS(reset_msd_ref(s));
+  s->rdf_meas = 0;
+  return MD_OK;
+}
+
+md_status set_state_impl(md_system* s, const double* pos, const double* vel, int on_device) {
+  const double* dpos = pos;
+  const double* dvel = vel;
+  const size_t bytes = sizeof(double) * 3 * (size_t)s->n_total;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(s->d_io, pos, bytes, cudaMemcpyHostToDevice, s->stream));
+    dpos = s->d_io;
+    if (vel) {
+      CK(cudaMemcpyAsync(s->d_io + 3 * s->n_total, vel, bytes, cudaMemcpyHostToDevice, s->stream));
+      dvel = s->d_io + 3 * s->n_total;
+    }
+  }
+  const int b = 256;
+  k_set_state<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(
+      s->mixed, s->n_total, s->ntot, s->d_reps, s->d_rep_of_caller, s->d_typ_caller, dpos, dvel, 0, s->d_pfx,
+      s->d_pq[0], s->d_velf, s->d_frcf, s->d_xbq, s->d_p4[0], s->d_veld, s->d_frcd, s->d_xbd, s->d_gid, s->d_typ,
+      s->d_img, s->d_nnb);
+  CK(cudaGetLastError());
+  return after_new_state(s);
+}
+
+md_status validate_table(int ntypes, const double* eps, const double* sigma, const double* rc, const double* L, int nrep,
+                         double skin) {
+  if (ntypes < 1 || ntypes > MD_MAXTYPES) return fail(nullptr, MD_ERR_INVALID_ARG, "ntypes must be in [1, 4]");
+  if (!eps || !sigma || !rc) return fail(nullptr, MD_ERR_INVALID_ARG, "eps, sigma and rc tables are required");
+  for (int a = 0; a < ntypes; ++a)
+    for (int b = 0; b < ntypes; ++b) {
+      const int t = a * ntypes + b, u = b * ntypes + a;
+      if (!(eps[t] > 0) || !(sigma[t] > 0) || !(rc[t] > 0))
+        return fail(nullptr, MD_ERR_INVALID_ARG, "eps, sigma and rc must be > 0");
+      if (eps[t] != eps[u] || sigma[t] != sigma[u] || rc[t] != rc[u])
+        return fail(nullptr, MD_ERR_INVALID_ARG, "eps, sigma and rc tables must be symmetric");
+      for (int r = 0; r < nrep; ++r)
+        if (!(rc[t] < 0.5 * L[r]))
+          return fail(nullptr, MD_ERR_INVALID_ARG, "every cutoff must be < L/2 (unique minimum image)");
+    }
+  if (!(skin >= 0)) return fail(nullptr, MD_ERR_INVALID_ARG, "skin must be >= 0");
+  return MD_OK;
+}
+
+md_status destroy_fail(md_system* s, md_status st) {
+  g_create_err = s->err;
+  md_destroy(s);
+  return st;
+}
+
+md_status tuning_ok(md_system* s, const md_tuning* t) {
+  const int T = t->threads_per_atom, b = t->block_size;
+  if (!(T == 1 || T == 2 || T == 4 || T == 8)) return fail(s, MD_ERR_INVALID_ARG, "threads_per_atom must be 1, 2, 4 or 8");
+  if (!(b == 128 || b == 256 || b == 512)) return fail(s, MD_ERR_INVALID_ARG, "block_size must be 128, 256 or 512");
+  if (b < 32 * T) return fail(s, MD_ERR_INVALID_ARG, "block_size must hold at least one 32-particle tile");
+  if (!(t->skin >= 0) || !(t->skin < 2.0)) return fail(s, MD_ERR_INVALID_ARG, "skin must be in [0, 2)");
+  for (int r = 0; r < s->nrep; ++r)
+    if (!(rc_max(s) < 0.5 * s->L_per[r])) return fail(s, MD_ERR_INVALID_ARG, "cutoff must be < L/2");
+  return MD_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, const uint8_t* types, int ntypes,
+                          const double* eps, const double* sigma, const double* rc, double mass, double skin,
+                          md_precision prec, void* stream, md_system** out) {
+  if (!out) return fail(nullptr, MD_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (nrep < 1 || !n_per || !L_per || !types) return fail(nullptr, MD_ERR_INVALID_ARG, "nrep >= 1 and arrays required");
+  if (prec != MD_PREC_FP64 && prec != MD_PREC_MIXED) return fail(nullptr, MD_ERR_INVALID_ARG, "unknown precision");
+  if (!(mass > 0)) return fail(nullptr, MD_ERR_INVALID_ARG, "mass must be > 0");
+  int64_t ntotal = 0;
+  for (int r = 0; r < nrep; ++r) {
+    if (n_per[r] < 2) return fail(nullptr, MD_ERR_INVALID_ARG, "every replica needs n >= 2");
+    if (!(L_per[r] > 0) || !std::isfinite(L_per[r])) return fail(nullptr, MD_ERR_INVALID_ARG, "box edge must be > 0");
+    ntotal += n_per[r];
+  }
+  if (ntotal > (int64_t)1 << 30) return fail(nullptr, MD_ERR_INVALID_ARG, "at most 2^30 particles");
+  CKS(validate_table(ntypes, eps, sigma, rc, L_per, nrep, skin));
+  for (int64_t g = 0; g < ntotal; ++g)
+    if (types[g] >= ntypes) return fail(nullptr, MD_ERR_INVALID_ARG, "type index out of range");
+
+  md_system* s = new md_system();
+  s->stream = (cudaStream_t)stream;
+  s->nrep = nrep;
+  s->ntypes = ntypes;
+  s->n_total = ntotal;
+  s->mixed = prec == MD_PREC_MIXED;
+  s->mass = mass;
+  s->tun.skin = skin;
+  for (int t = 0; t < ntypes * ntypes; ++t) {
+    s->eps[t] = eps[t];
+    s->sig[t] = sigma[t];
+    s->rc[t] = rc[t];
+  }
+  if (const char* e = std::getenv("KAMD_BARRIER_TIMEOUT_MS")) s->timeout_ns = (unsigned long long)std::atoll(e) * 1000000ull;
+  cudaError_t ce = cudaGetDevice(&s->device);
+  if (ce != cudaSuccess) return destroy_fail(s, cuda_fail(s, ce, "cudaGetDevice"));
+  int major = 0, minor = 0, coop = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, s->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, s->device);
+  cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+  if (major != 10 || minor != 3 || !coop) {
+    s->err = "this library is built for sm_103a (GB300) with cooperative launch";
+    return destroy_fail(s, MD_ERR_NOT_SUPPORTED);
+  }
+  // replicas: slot ranges padded to whole 32-particle tiles
+  s->n_per.assign(n_per, n_per + nrep);
+  s->L_per.assign(L_per, L_per + nrep);
+  s->reps.resize(nrep);
+  std::vector<int32_t> tile_rep;
+  std::vector<int32_t> rep_of(ntotal);
+  int64_t off = 0, o0 = 0;
+  for (int r = 0; r < nrep; ++r) {
+    RepDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.off = off;
+    R.out0 = o0;
+    R.n = (int32_t)n_per[r];
+    R.ntiles = (int32_t)((n_per[r] + 31) / 32);
+    R.tile0 = (int32_t)(off / 32);
+    R.L = L_per[r];
+    R.invL = 1.0 / L_per[r];
+    R.fx64 = 18446744073709551616.0 / L_per[r];
+    R.Lf = (float)L_per[r];
+    R.fxs = (float)(L_per[r] / 4294967296.0);
+    R.fx64f = (float)R.fx64;
+    s->reps[r] = R;
+    s->out0.push_back(o0);
+    for (int t = 0; t < R.ntiles; ++t) tile_rep.push_back(r);
+    for (int64_t k = 0; k < n_per[r]; ++k) rep_of[o0 + k] = r;
+    off += (int64_t)R.ntiles * 32;
+    o0 += n_per[r];
+  }
+  s->ntot = off;
+  s->ntiles = (int)(off / 32);
+  layout_cells(s);
+  md_status st;
+  const size_t nt = (size_t)s->ntot;
+#define AL(ptr, cnt)                                   \
+  do {                                                 \
+    st = dalloc(s, &(ptr), (cnt));                     \
+    if (st != MD_OK) return destroy_fail(s, st);       \
+  } while (0)
+  AL(s->d_reps, (size_t)nrep);
+  AL(s->d_tile_rep, (size_t)s->ntiles);
+  AL(s->d_ctl, 1);
+  if (s->mixed) {
+    AL(s->d_pfx, 3 * nt);
+    AL(s->d_pq[0], nt);
+    AL(s->d_pq[1], nt);
+    AL(s->d_velf, 3 * nt);
+    AL(s->d_frcf, 3 * nt);
+    AL(s->d_xbq, nt);
+    AL(s->d_tpfx, 3 * nt);
+    float* tv = nullptr;
+    float* tf = nullptr;
+    AL(tv, 3 * nt);
+    AL(tf, 3 * nt);
+    s->d_tvel = tv;
+    s->d_tfrc = tf;
+  } else {
+    AL(s->d_p4[0], nt);
+    AL(s->d_p4[1], nt);
+    AL(s->d_veld, 3 * nt);
+    AL(s->d_frcd, 3 * nt);
+    AL(s->d_xbd, nt);
+    AL(s->d_tp4, nt);
+    double* tv = nullptr;
+    double* tf = nullptr;
+    AL(tv, 3 * nt);
+    AL(tf, 3 * nt);
+    s->d_tvel = tv;
+    s->d_tfrc = tf;
+  }
+  AL(s->d_gid, nt);
+  AL(s->d_typ, nt);
+  AL(s->d_img, 3 * nt);
+  AL(s->d_tgid, nt);
+  AL(s->d_ttyp, nt);
+  AL(s->d_timg, 3 * nt);
+  AL(s->d_cellof, nt);
+  AL(s->d_scat, nt);
+  AL(s->d_nnb, nt);
+  AL(s->d_part[0], (size_t)s->ntiles * MD_NPART);
+  AL(s->d_part[1], (size_t)s->ntiles * MD_NPART);
+  AL(s->d_typ_caller, (size_t)ntotal);
+  AL(s->d_rep_of_caller, (size_t)ntotal);
+  AL(s->d_msd_ref, 3 * (size_t)ntotal);
+  AL(s->d_io, 6 * (size_t)ntotal);
+  AL(s->d_io_i, 3 * (size_t)ntotal);
+  AL(s->d_msd_part, (size_t)s->ntiles * MD_NPART);
+  AL(s->d_count, 1);
+#undef AL
+  st = alloc_cells_and_list(s, list_capacity(s));
+  if (st != MD_OK) return destroy_fail(s, st);
+  ce = cudaMemcpyAsync(s->d_tile_rep, tile_rep.data(), 4 * tile_rep.size(), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(s->d_rep_of_caller, rep_of.data(), 4 * rep_of.size(), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_typ_caller, types, (size_t)ntotal, cudaMemcpyHostToDevice, s->stream);
+  if (ce != cudaSuccess) return destroy_fail(s, cuda_fail(s, ce, "cudaMemcpyAsync"));
+  st = upload_reps(s);
+  if (st == MD_OK) st = upload_ctl(s);
+  if (st == MD_OK) st = configure_grid(s);
+  if (st != MD_OK) return destroy_fail(s, st);
+  ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return destroy_fail(s, cuda_fail(s, ce, "cudaStreamSynchronize"));
+  *out = s;
+  return MD_OK;
+}
+
+md_status md_create(int64_t n, const uint8_t* types, int ntypes, double L, const double* eps, const double* sigma,
+                    const double* rc, double mass, double skin, md_precision prec, void* stream, md_system** out) {
+  return md_create_batch(1, &n, &L, types, ntypes, eps, sigma, rc, mass, skin, prec, stream, out);
+}
+
+md_status md_set_state(md_system* s, const double* pos, const double* vel, int on_device) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!pos) return fail(s, MD_ERR_INVALID_ARG, "pos must not be NULL");
+  return set_state_impl(s, pos, vel, on_device);
+}
+
+md_status md_get_state(md_system* s, double* pos, double* vel, int32_t* images, int on_device) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state: call md_set_state or md_init_lattice first");
+  const size_t n3 = 3 * (size_t)s->n_total;
+  double* dp = on_device ? pos : (pos ? s->d_io : nullptr);
+  double* dv = on_device ? vel : (vel ? s->d_io + n3 : nullptr);
+  int32_t* di = on_device ? images : (images ? s->d_io_i : nullptr);
+  CKS(download_ctl(s));
+  const int b = 256;
+  k_get_state<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, s->d_reps, s->d_tile_rep, s->ctl.cur,
+                                                           s->d_pfx, s->d_velf, s->d_p4[s->ctl.cur], s->d_veld,
+                                                           s->d_gid, s->d_img, dp, dv, di);
+  CK(cudaGetLastError());
+  if (!on_device) {
+    if (pos) CK(cudaMemcpyAsync(pos, dp, 8 * n3, cudaMemcpyDeviceToHost, s->stream));
+    if (vel) CK(cudaMemcpyAsync(vel, dv, 8 * n3, cudaMemcpyDeviceToHost, s->stream));
+    if (images) CK(cudaMemcpyAsync(images, di, 4 * n3, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  return MD_OK;
+}
+
+md_status md_init_lattice(md_system* s, const double* T0, double jitter, uint64_t seed) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!T0) return fail(s, MD_ERR_INVALID_ARG, "T0 must not be NULL");
+  if (!(jitter >= 0)) return fail(s, MD_ERR_INVALID_ARG, "jitter must be >= 0");
+  for (int r = 0; r < s->nrep; ++r)
+    if (!(T0[r] >= 0)) return fail(s, MD_ERR_INVALID_ARG, "T0 must be >= 0");
+  const int b = 256;
+  k_lattice<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(s->n_total, s->d_reps, s->d_rep_of_caller, jitter, seed,
+                                                            s->d_io);
+  CK(cudaGetLastError());
+  CKS(set_state_impl(s, s->d_io, nullptr, 1));
+  CKS(download_reps(s));
+  for (int r = 0; r < s->nrep; ++r) s->reps[r].T_target = T0[r];
+  CKS(upload_reps(s));
+  CKS(run_op(s, MD_OP_INITVEL, MD_KIND_NVE, 0.0, 0, 0, seed, 0, 0, nullptr));
+  return MD_OK;
+}
+
+md_status md_forces(md_system* s, double* f, double* pe, double* virial, int on_device) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state: call md_set_state or md_init_lattice first");
+  CKS(run_op(s, MD_OP_FORCES, MD_KIND_NVE, 0.0, 0, 0, 0, 0, 0, nullptr));
+  if (f) {
+    double* df = on_device ? f : s->d_io;
+    const int b = 256;
+    k_get_forces<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, s->d_reps, s->d_tile_rep, s->d_frcf,
+                                                              s->d_frcd, s->d_gid, df);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(f, df, 24 * (size_t)s->n_total, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CKS(download_reps(s));
+  for (int r = 0; r < s->nrep; ++r) {
+    if (pe) pe[r] = s->reps[r].pe;
+    if (virial) virial[r] = s->reps[r].vir;
+  }
+  return MD_OK;
+}
+
+static md_status step_common(md_system* s, int kind, double dt, int64_t nsteps, int64_t nstep_boltz, uint64_t seed,
+                             md_thermo* log, int64_t log_every) {
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state: call md_set_state or md_init_lattice first");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(s, MD_ERR_INVALID_ARG, "dt must be > 0");
+  if (nsteps < 0) return fail(s, MD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (log && log_every <= 0) return fail(s, MD_ERR_INVALID_ARG, "log_every must be > 0 when log is given");
+  const int64_t nlog = (log && log_every > 0) ? nsteps / log_every : 0;
+  CKS(ensure_thermo(s, nlog * s->nrep));
+  int64_t done = 0;
+  md_status st = run_op(s, MD_OP_STEPS, kind, dt, nsteps, nstep_boltz, seed, log ? log_every : 0, nlog, &done);
+  if (st != MD_OK) return st;
+  if (nlog > 0) {
+    CK(cudaMemcpyAsync(log, s->d_thermo, sizeof(ThermoDev) * nlog * s->nrep, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  return MD_OK;
+}
+
+md_status md_step_nve(md_system* s, double dt, int64_t nsteps, md_thermo* log, int64_t log_every) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  return step_common(s, MD_KIND_NVE, dt, nsteps, 0, 0, log, log_every);
+}
+
+md_status md_step_nvt(md_system* s, double dt, int64_t nsteps, const double* T_target, md_thermostat kind, double param,
+                      uint64_t seed, md_thermo* log, int64_t log_every) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!T_target) return fail(s, MD_ERR_INVALID_ARG, "T_target must not be NULL");
+  for (int r = 0; r < s->nrep; ++r)
+    if (!(T_target[r] >= 0) || !std::isfinite(T_target[r])) return fail(s, MD_ERR_INVALID_ARG, "T_target must be >= 0");
+  int k;
+  int64_t nb = 0;
+  if (kind == MD_NVT_NOSE_HOOVER || kind == MD_NVT_NOSE_HOOVER_EXACT) {
+    if (!(param > 0)) return fail(s, MD_ERR_INVALID_ARG, "Nose-Hoover needs tau > 0");
+    for (int r = 0; r < s->nrep; ++r)
+      if (!(T_target[r] > 0)) return fail(s, MD_ERR_INVALID_ARG, "Nose-Hoover needs T_target > 0");
+    k = kind == MD_NVT_NOSE_HOOVER ? MD_KIND_NH : MD_KIND_NH_EXACT;
+  } else if (kind == MD_NVT_RESAMPLE) {
+    nb = (int64_t)param;
+    if (nb < 1) return fail(s, MD_ERR_INVALID_ARG, "resampling needs nstep_boltz >= 1");
+    k = MD_KIND_RESAMPLE;
+  } else {
+    return fail(s, MD_ERR_INVALID_ARG, "unknown thermostat");
+  }
+  CKS(download_reps(s));
+  for (int r = 0; r < s->nrep; ++r) {
+    RepDev& R = s->reps[r];
+    R.T_target = T_target[r];
+    if (k != MD_KIND_RESAMPLE) R.Q = 3.0 * R.n * T_target[r] * param * param;
+  }
+  CKS(upload_reps(s));
+  return step_common(s, k, dt, nsteps, nb, seed, log, log_every);
+}
+
+md_status md_rdf(md_system* s, double dr, int64_t nbins, double* g, int reset) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
+  if (s->ntypes != 2) return fail(s, MD_ERR_INVALID_ARG, "md_rdf needs a 2-type system");
+  if (!(dr > 0) || nbins < 1) return fail(s, MD_ERR_INVALID_ARG, "dr > 0 and nbins >= 1 required");
+  for (int r = 0; r < s->nrep; ++r)
+    if (dr * nbins > 0.5 * s->L_per[r] * (1 + 1e-12)) return fail(s, MD_ERR_INVALID_ARG, "nbins*dr must be <= L/2");
+  if (reset || !s->d_rdf || nbins != s->rdf_nbins || dr != s->rdf_dr) {
+    dfree(s->d_rdf);
+    CKS(dalloc(s, &s->d_rdf, (size_t)s->nrep * 3 * nbins));
+    s->rdf_nbins = nbins;
+    s->rdf_dr = dr;
+    s->rdf_meas = 0;
+  }
+  // the histogram walks the cell lists of the last build: make them current
+  CKS(download_ctl(s));
+  if (s->ctl.pending & MD_FLAG_REBUILD) CKS(run_op(s, MD_OP_REBUILD, MD_KIND_NVE, 0, 0, 0, 0, 0, 0, nullptr));
+  CKS(download_ctl(s));
+  const int b = 128;
+  k_rdf<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, (int)nbins, dr, s->tun.skin, s->d_reps, s->d_tile_rep,
+                                                     s->ctl.cur, s->d_pq[s->ctl.cur], s->d_pfx, s->d_p4[s->ctl.cur],
+                                                     s->d_typ, s->d_cstart, s->d_rdf);
+  CK(cudaGetLastError());
+  s->rdf_meas += 1;
+  if (g) {
+    std::vector<unsigned long long> h((size_t)s->nrep * 3 * nbins);
+    CK(cudaMemcpyAsync(h.data(), s->d_rdf, 8 * h.size(), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::vector<uint8_t> types(s->n_total);
+    CK(cudaMemcpy(types.data(), s->d_typ_caller, s->n_total, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < 3 * nbins; ++k) g[k] = 0.0;
+    for (int r = 0; r < s->nrep; ++r) {
+      int64_t na = 0, nb = 0;
+      for (int64_t q = 0; q < s->n_per[r]; ++q) (types[s->out0[r] + q] == 0 ? na : nb) += 1;
+      const double V = s->L_per[r] * s->L_per[r] * s->L_per[r];
+      for (int64_t k = 0; k < nbins; ++k) {
+        const double shell = 4.0 / 3.0 * M_PI * (std::pow((double)(k + 1), 3) - std::pow((double)k, 3)) * dr * dr * dr;
+        const unsigned long long* hr = h.data() + (size_t)r * 3 * nbins;
+        const double m = (double)s->rdf_meas * s->nrep;
+        if (na > 1) g[k] += hr[k] / shell * V / ((double)na * (na - 1)) / m;
+        if (nb > 1) g[nbins + k] += hr[nbins + k] / shell * V / ((double)nb * (nb - 1)) / m;
+        if (na > 0 && nb > 0) g[2 * nbins + k] += hr[2 * nbins + k] / shell * V / ((double)na * nb) / m;
+      }
+    }
+  }
+  return MD_OK;
+}
+
+md_status md_msd(md_system* s, double* msd_per_type, int reset_reference) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
+  CKS(download_ctl(s));
+  if (reset_reference) CKS(reset_msd_ref(s));
+  const int b = 256;
+  k_msd_tiles<<<blocks_for((int64_t)s->ntiles * 32, b), b, 0, s->stream>>>(
+      s->mixed, s->ntiles, s->ntypes, s->ntot, s->d_reps, s->d_tile_rep, s->d_pfx, s->d_p4[s->ctl.cur], s->d_gid,
+      s->d_typ, s->d_img, s->d_msd_ref, s->d_msd_part);
+  CK(cudaGetLastError());
+  k_msd_final<<<1, 32, 0, s->stream>>>(s->ntiles, s->ntypes, s->d_msd_part, s->d_io);
+  CK(cudaGetLastError());
+  if (msd_per_type) CK(cudaMemcpyAsync(msd_per_type, s->d_io, 8 * s->ntypes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MD_OK;
+}
+
+md_status md_set_tuning(md_system* s, const md_tuning* t) {
+  if (!s || !t) return fail(s, MD_ERR_INVALID_ARG, "NULL argument");
+  CKS(tuning_ok(s, t));
+  CKS(download_reps(s));
+  s->tun = *t;
+  layout_cells(s);
+  for (auto& R : s->reps) R.want_rebuild = 1;
+  CKS(upload_reps(s));
+  CKS(alloc_cells_and_list(s, list_capacity(s)));
+  CKS(configure_grid(s));
+  CKS(download_ctl(s));
+  s->ctl.pending |= MD_FLAG_REBUILD;
+  CKS(upload_ctl(s));
+  return MD_OK;
+}
+
+md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* best, double* seconds_per_step) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
+  if (!(dt > 0) || probe_steps < 1) return fail(s, MD_ERR_INVALID_ARG, "dt > 0 and probe_steps >= 1 required");
+  // save the state (caller order, device) and the per-replica bath state
+  const size_t n3 = 3 * (size_t)s->n_total;
+  double* saved = nullptr;
+  int32_t* saved_img = nullptr;
+  CKS(dalloc(s, &saved, 2 * n3));
+  CKS(dalloc(s, &saved_img, n3));
+  md_status st = md_get_state(s, saved, saved + n3, saved_img, 1);
+  if (st != MD_OK) { dfree(saved); dfree(saved_img); return st; }
+  CKS(download_reps(s));
+  const std::vector<RepDev> saved_reps = s->reps;
+  const int64_t saved_step = s->ctl.step;
+  const md_tuning start = s->tun;
+  md_tuning bt = start;
+  float bms = 1e30f;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int Ts[4] = {1, 2, 4, 8};
+  const int Bs[3] = {128, 256, 512};
+  const double Ss[3] = {0.2, 0.3, 0.4};
+  for (int ti = 0; ti < 4 && st == MD_OK; ++ti)
+    for (int bi = 0; bi < 3 && st == MD_OK; ++bi)
+      for (int si = 0; si < 3 && st == MD_OK; ++si) {
+        md_tuning c{Ts[ti], Bs[bi], Ss[si]};
+        if (c.block_size < 32 * c.threads_per_atom) continue;
+        if (tuning_ok(s, &c) != MD_OK) continue;
+        st = md_set_tuning(s, &c);
+        if (st == MD_OK) st = set_state_impl(s, saved, saved + n3, 1);
+        if (st == MD_OK) st = md_step_nve(s, dt, std::max<int64_t>(probe_steps / 4, 1), nullptr, 0);
+        if (st != MD_OK) break;
+        cudaEventRecord(e0, s->stream);
+        st = md_step_nve(s, dt, probe_steps, nullptr, 0);
+        cudaEventRecord(e1, s->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == MD_OK && ms < bms) { bms = ms; bt = c; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  md_status st2 = md_set_tuning(s, st == MD_OK ? &bt : &start);
+  if (st2 == MD_OK) st2 = set_state_impl(s, saved, saved + n3, 1);
+  if (st2 == MD_OK) {
+    const int b = 256;
+    k_set_images<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(s->n_total, s->ntot, s->d_reps, s->d_rep_of_caller,
+                                                                 saved_img, s->d_img);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) st2 = cuda_fail(s, ce, "k_set_images");
+  }
+  if (st2 == MD_OK) st2 = download_reps(s);
+  if (st2 == MD_OK) {
+    for (int r = 0; r < s->nrep; ++r) {
+      RepDev& R = s->reps[r];
+      const RepDev& O = saved_reps[r];
+      R.T_target = O.T_target; R.Q = O.Q; R.xi = O.xi; R.g = O.g; R.lns = O.lns; R.lns_next = O.lns_next;
+      R.xi_a = O.xi_a; R.rebuilds = O.rebuilds;
+    }
+    st2 = upload_reps(s);
+  }
+  if (st2 == MD_OK) {
+    s->ctl.step = saved_step;
+    st2 = upload_ctl(s);
+  }
+  if (st2 == MD_OK) st2 = reset_msd_ref(s);
+  cudaStreamSynchronize(s->stream);
+  s->bytes -= (3 * n3) * 8;
+  dfree(saved);
+  dfree(saved_img);
+  if (st != MD_OK) return st;
+  if (st2 != MD_OK) return st2;
+  if (best) *best = bt;
+  if (seconds_per_step) *seconds_per_step = (double)bms * 1e-3 / (double)probe_steps;
+  return MD_OK;
+}
+
+md_status md_get_tuning(const md_system* s, md_tuning* t) {
+  if (!s || !t) return MD_ERR_INVALID_ARG;
+  *t = s->tun;
+  return MD_OK;
+}
+
+md_status md_get_info(md_system* s, md_info* info) {
+  if (!s || !info) return fail(s, MD_ERR_INVALID_ARG, "NULL argument");
+  CKS(download_reps(s));
+  CKS(download_ctl(s));
+  std::memset(info, 0, sizeof(*info));
+  info->n_total = s->n_total;
+  info->n_replicas = s->nrep;
+  info->grid_blocks = s->grid;
+  info->steps_done = s->ctl.step;
+  for (const auto& R : s->reps) {
+    info->rebuilds += R.rebuilds;
+    info->list_entries += R.list_entries;
+    info->all_pairs_replicas += R.nc == 0;
+  }
+  info->list_capacity = (int64_t)s->maxrows * s->tun.threads_per_atom;
+  info->device_bytes = (int64_t)s->bytes;
+  info->precision = s->mixed ? MD_PREC_MIXED : MD_PREC_FP64;
+  return MD_OK;
+}
+
+md_status md_count_pairs(md_system* s, int64_t* pairs) {
+  if (!s || !pairs) return fail(s, MD_ERR_INVALID_ARG, "NULL argument");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
+  CKS(download_ctl(s));
+  if (s->ctl.pending & MD_FLAG_REBUILD) CKS(run_op(s, MD_OP_REBUILD, MD_KIND_NVE, 0, 0, 0, 0, 0, 0, nullptr));
+  CKS(download_ctl(s));
+  KParams p = make_params(s);
+  float rc2f[16];
+  double rc2d[16];
+  for (int t = 0; t < 16; ++t) {
+    rc2f[t] = p.tab_f[t][0];
+    rc2d[t] = p.tab_d[t][0];
+  }
+  CK(cudaMemcpyAsync(s->d_io, rc2d, sizeof rc2d, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->d_io + 16, rc2f, sizeof rc2f, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->d_count, 0, 8, s->stream));
+  const int b = 256;
+  k_count_pairs<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(
+      s->mixed, s->ntot, s->tun.threads_per_atom, s->maxrows, s->ntypes, s->d_reps, s->d_tile_rep, s->ctl.cur,
+      s->d_pq[s->ctl.cur], s->d_p4[s->ctl.cur], s->d_nbr, s->d_nnb, (const float*)(s->d_io + 16), s->d_io, s->d_count);
+  CK(cudaGetLastError());
+  unsigned long long c = 0;
+  CK(cudaMemcpyAsync(&c, s->d_count, 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  *pairs = (int64_t)(c / 2);
+  return MD_OK;
+}
+
+const char* md_last_error(const md_system* s) {
+  if (!s) return g_create_err.c_str();
+  return s->err.c_str();
+}
+
+void md_destroy(md_system* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  dfree(s->d_reps); dfree(s->d_tile_rep); dfree(s->d_ctl);
+  dfree(s->d_pfx); dfree(s->d_pq[0]); dfree(s->d_pq[1]); dfree(s->d_velf); dfree(s->d_frcf); dfree(s->d_xbq);
+  dfree(s->d_p4[0]); dfree(s->d_p4[1]); dfree(s->d_veld); dfree(s->d_frcd); dfree(s->d_xbd);
+  dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
+  dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
+  dfree(s->d_timg);
+  dfree(s->d_cellof); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_scat);
+  dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
+  dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
+  dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// md_internal.cuh -- definitions shared by the library's translation units.
+//
+// Memory layout in HBM (all arrays packed over replicas; each replica owns
+// a contiguous slot range starting at a multiple of 32 and padded to a
+// multiple of 32, so every 32-slot tile belongs to exactly one replica):
+//
+//   mixed precision                       all-FP64
+//   pfx   u64  [3][ntot]  fixed point     p4[2] double4_32a [ntot]  (x,y,z,type)
+//   pq[2] uint4 [ntot] (x,y,z hi32,type)  -- gather copy = master, double-buffered
+//   velf  f32  [3][ntot]                  veld f64 [3][ntot]
+//   frcf  f32  [3][ntot]                  frcd f64 [3][ntot]
+//   xbq   uint4 [ntot] (position at the   xbd  double4_32a [ntot]
+//         last list build, hi32)
+//   gid i32 [ntot] caller index; typ u8 [ntot]; img i32 [3][ntot] image counters
+//   nbr i32 [ntiles][maxrows][32*T]: entry k of particle a of a tile sits at
+//       row k/T, column a*T + k%T, so the T lanes that share a particle read
+//       consecutive words and a warp reads 128 contiguous bytes per row.
+//   cells: ccount/ccursor [ncells], cstart [ncells + nrep], cellof/scat [ntot]
+//
+// Fixed-point positions: u = x/L * 2^64 (mod 2^64). Wrapping into the box is
+// the natural overflow of the integer; the minimum-image difference of two
+// particles is the signed 32-bit difference of their top words, exact.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define MD_TILE 32
+#define MD_MAXTYPES 4
+#define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
+
+// pending/commit flag bits (grid-uniform decisions)
+#define MD_FLAG_REBUILD 1
+#define MD_FLAG_OVERFLOW 2
+#define MD_FLAG_UNSTABLE 4
+#define MD_FLAG_TIMEOUT 8
+
+enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3 };
+enum { MD_KIND_NVE = 0, MD_KIND_NH = 1, MD_KIND_RESAMPLE = 2, MD_KIND_NH_EXACT = 3 };
+
+// Per-replica description and state (device resident, one per replica).
+struct RepDev {
+  int64_t off;      // first slot (multiple of 32)
+  int64_t out0;     // offset of this replica in caller order
+  int64_t cell0;    // first cell in the packed cell arrays
+  int64_t cs0;      // first cstart entry (= cell0 + replica index)
+  int32_t n;        // particles
+  int32_t ntiles;   // slots / 32
+  int32_t tile0;    // first tile
+  int32_t nc;       // cells per edge (0: list built by an all-pairs scan)
+  double L, invL;
+  double fx64;      // 2^64 / L
+  float Lf, fxs;    // L, L / 2^32
+  float fx64f;      // 2^64 / L
+  float cellw;      // L / nc
+  // bath
+  double T_target, Q;
+  double xi, g, lns, lns_next, xi_a;
+  // last reductions
+  double pe, ke, vir, px, py, pz;
+  // resampling
+  double vmean[3], vscale;
+  int32_t want_rebuild, doing_rebuild;
+  int64_t rebuilds;
+  int64_t list_entries;
+};
+
+// Grid barrier and launch-wide control block.
+struct CtlDev {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int pending;          // flags raised during a phase (atomicOr)
+  int snap[2];          // pending as seen by the last arriver, per barrier parity
+  int cur;              // parity of the current gather buffer
+  int drifted;          // 1: positions at t+dt while velocities/forces are at t
+  int forces_valid;
+  int64_t step;         // global step counter
+  int64_t steps_done;   // steps completed by the current/last launch
+  int err_where;        // phase id where a barrier timed out
+  int pad;
+};
+
+struct ThermoDev {  // layout identical to md_thermo
+  int64_t step;
+  double T, pe_per_n, ke_per_n, etot_per_n, virial, h_nh, xi;
+};
+
+struct KParams {
+  // sizes
+  int nrep;
+  int ntypes;
+  int64_t ntot;        // slots
+  int ntiles;
+  int T;               // lanes per particle
+  int maxrows;         // list rows per tile (capacity per particle = maxrows*T)
+  // interaction tables, index a*ntypes+b
+  float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps
+  float vsh_f[MD_MAXTYPES * MD_MAXTYPES];      // V(rc)
+  float rl2_f[MD_MAXTYPES * MD_MAXTYPES];      // (rc + skin)^2
+  double tab_d[MD_MAXTYPES * MD_MAXTYPES][4];
+  double vsh_d[MD_MAXTYPES * MD_MAXTYPES];
+  double rl2_d[MD_MAXTYPES * MD_MAXTYPES];
+  double mass, inv_mass;
+  double skin_half2;   // (skin/2)^2
+  // operation
+  int op;
+  int kind;
+  double dt;
+  int64_t nsteps;      // steps to run in this launch
+  int64_t nstep_boltz;
+  uint64_t seed;
+  int64_t log_every;
+  int64_t log_step0;   // steps completed in this call before this launch
+  int64_t log_cap;     // records per replica the log can hold
+  ThermoDev* thermo;
+  unsigned long long timeout_ns;
+  // state
+  RepDev* reps;
+  int32_t* tile_rep;
+  CtlDev* ctl;
+  uint64_t* pfx;
+  uint4* pq[2];
+  float* velf;
+  float* frcf;
+  uint4* xbq;
+  double4_32a* p4[2];
+  double* veld;
+  double* frcd;
+  double4_32a* xbd;
+  int32_t* gid;
+  uint8_t* typ;
+  int32_t* img;
+  // permutation scratch
+  uint64_t* t_pfx;
+  double4_32a* t_p4;
+  void* t_vel;
+  void* t_frc;
+  int32_t* t_gid;
+  uint8_t* t_typ;
+  int32_t* t_img;
+  // cells and list
+  int32_t* cellof;
+  int32_t* ccount;
+  int32_t* cstart;
+  int32_t* ccursor;
+  int32_t* scat;
+  int32_t* nbr;
+  int32_t* nnb;
+  // reductions
+  double* part[2];     // [ntiles][MD_NPART]
+};
+
+// Host-side launchers (md_kernel.cu).
+cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s);
+cudaError_t md_occupancy(bool mixed, int block, int* blocks_per_sm);

@@ -1,0 +1,874 @@
+// md_kernel.cu -- the persistent sm_103a kernel that advances every replica.
+//
+// One cooperative launch runs a whole md_step call: all CTAs stay resident
+// and meet at a bounded grid barrier between phases. Per time step:
+//
+//   force phase   F_i = sum_j 48 eps_ab (sigma^12/r^14 - sigma^6/(2 r^8)) r_ij
+//                 (Eq. (KAFix), cutoff of Eq. (VshiftedKALJ), minimum image of
+//                 Sec. "Periodic boundary conditions"), gathered over a full
+//                 Verlet list by T lanes per particle (no atomics), then the
+//                 velocity update (Eq. (velVerletVel), or Eq. (ridotKVLRoman) /
+//                 (ridotsolved) under Nose-Hoover), per-tile FP64 partial sums
+//                 of PE, KE, virial, momentum, and -- for NVE steps -- the next
+//                 position update (Eq. (velVerletPos)) fused in.
+//   barrier
+//   reduce        per replica, fixed-order sum of tile partials; Nose-Hoover
+//                 xi, ln s updates (Eqs. (Noseupdate_lns), (Noseupdate_xiapprox),
+//                 (FoxAndersen_ydottplush)); thermo record.
+//   [Nose-Hoover: barrier, position update Eq. (Noseupdate_ri), barrier]
+//   [resampling step: Maxwell-Boltzmann draw, reduce, centre+rescale+drift]
+//   [rebuild when any particle moved > skin/2: cell count, scan, scatter,
+//    in-cell rank sort by caller index, permute, Verlet-list build]
+//
+// All decisions that change the phase sequence are read from a snapshot the
+// barrier takes, so every CTA takes the same branch. Every barrier wait is
+// bounded in time; on expiry the kernel raises MD_FLAG_TIMEOUT and returns.
+#include "md_device.cuh"
+#include "md_internal.cuh"
+
+namespace kamd {
+
+enum { KICK_NONE = 0, KICK_VV = 1, KICK_NH = 2, KICK_NH_EXACT = 3 };
+enum { RED_FORCES = 0, RED_KE = 1, RED_STEP = 2, RED_RESAMPLE = 3 };
+
+struct Shared {
+  float4 tabf[MD_MAXTYPES * MD_MAXTYPES];
+  float vshf[MD_MAXTYPES * MD_MAXTYPES];
+  float rl2f[MD_MAXTYPES * MD_MAXTYPES];
+  double4_32a tabd[MD_MAXTYPES * MD_MAXTYPES];
+  double vshd[MD_MAXTYPES * MD_MAXTYPES];
+  double rl2d[MD_MAXTYPES * MD_MAXTYPES];
+  double red[16][MD_NPART];
+  int scan[32];
+  int snap;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned vload_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
+__device__ __forceinline__ int vload_i32(const int* p) { return *(volatile const int*)p; }
+
+// Grid barrier with a time limit. Returns the pending-flag snapshot taken by
+// the last CTA to arrive (identical for every CTA), or -1 after a timeout.
+__device__ int grid_sync(const KParams& p, Shared& sh, int where) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CtlDev* c = p.ctl;
+    const unsigned g = vload_u32(&c->bar_gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    int res = -1;
+    if (arrived == gridDim.x - 1) {
+      c->bar_count = 0;
+      const int pend = atomicOr(&c->pending, 0);
+      c->snap[(g + 1) & 1] = pend;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+      res = pend;
+    } else {
+      const unsigned long long t0 = globaltimer();
+      unsigned it = 0;
+      while (true) {
+        if (vload_u32(&c->bar_gen) != g) {
+          __threadfence();
+          res = vload_i32(&c->snap[(g + 1) & 1]);
+          break;
+        }
+        if (((++it) & 63u) == 0) {
+          if (vload_i32(&c->pending) & MD_FLAG_TIMEOUT) break;
+          if (globaltimer() - t0 > p.timeout_ns || it > (1u << 30)) {
+            atomicOr(&c->pending, MD_FLAG_TIMEOUT);
+            atomicExch(&c->err_where, where);
+            break;
+          }
+        }
+        __nanosleep(32);
+      }
+    }
+    sh.snap = res;
+  }
+  __syncthreads();
+  return sh.snap;
+}
+
+__device__ __forceinline__ void raise_flag(const KParams& p, int f) {
+  if (!(vload_i32(&p.ctl->pending) & f)) atomicOr(&p.ctl->pending, f);
+}
+
+// ------------------------------------------------------------------ drift
+
+// Position update of one particle. Mixed: FP32 increment added to the 64-bit
+// fixed-point coordinate (wrap = integer overflow, image counted from the
+// carry). FP64: double increment, wrap into [0, L).
+template <bool MIX>
+__device__ __forceinline__ void drift_atom(const KParams& p, const RepDev& R, int64_t i, int cur,
+                                           double vx, double vy, double vz, double ax, double ay, double az,
+                                           double xi, uint32_t type) {
+  const int64_t nt = p.ntot;
+  if constexpr (MIX) {
+    const float dt = (float)p.dt, hdt2 = 0.5f * (float)p.dt * (float)p.dt, xif = (float)xi;
+    const float fv[3] = {(float)vx, (float)vy, (float)vz};
+    const float fa[3] = {(float)ax, (float)ay, (float)az};
+    float d[3];
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = fmaf(fv[c], dt, (fa[c] - xif * fv[c]) * hdt2);
+      bad |= !(fabsf(d[c]) < 0.25f * R.Lf);
+    }
+    if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
+    uint32_t hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint64_t u = p.pfx[c * nt + i];
+      const long long du = __float2ll_rn(d[c] * R.fx64f);
+      const uint64_t un = u + (uint64_t)du;
+      if (du > 0 && un < u) p.img[c * nt + i] += 1;
+      else if (du < 0 && un > u) p.img[c * nt + i] -= 1;
+      p.pfx[c * nt + i] = un;
+      hi[c] = (uint32_t)(un >> 32);
+    }
+    p.pq[cur ^ 1][i] = make_uint4(hi[0], hi[1], hi[2], type);
+    const uint4 xb = p.xbq[i];
+    const float ex = (float)(int)(hi[0] - xb.x) * R.fxs;
+    const float ey = (float)(int)(hi[1] - xb.y) * R.fxs;
+    const float ez = (float)(int)(hi[2] - xb.z) * R.fxs;
+    if (ex * ex + ey * ey + ez * ez > (float)p.skin_half2) {
+      p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
+      raise_flag(p, MD_FLAG_REBUILD);
+    }
+  } else {
+    const double dt = p.dt, hdt2 = 0.5 * p.dt * p.dt;
+    double4_32a x = p.p4[cur][i];
+    double d[3] = {vx * dt + (ax - xi * vx) * hdt2, vy * dt + (ay - xi * vy) * hdt2, vz * dt + (az - xi * vz) * hdt2};
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bad |= !(fabs(d[c]) < 0.25 * R.L);
+    if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
+    double xs[3] = {x.x + d[0], x.y + d[1], x.z + d[2]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
+      else if (xs[c] < 0.0) {
+        xs[c] += R.L; p.img[c * nt + i] -= 1;
+        if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
+      }
+    }
+    p.p4[cur ^ 1][i] = make_double4_32a(xs[0], xs[1], xs[2], x.w);
+    const double4_32a xb = p.xbd[i];
+    double e[3] = {xs[0] - xb.x, xs[1] - xb.y, xs[2] - xb.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (e[c] > 0.5 * R.L) e[c] -= R.L;
+      else if (e[c] < -0.5 * R.L) e[c] += R.L;
+    }
+    if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] > p.skin_half2) {
+      p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
+      raise_flag(p, MD_FLAG_REBUILD);
+    }
+  }
+}
+
+template <bool MIX>
+__device__ __forceinline__ void load_va(const KParams& p, int64_t i, double v[3], double a[3]) {
+  const int64_t nt = p.ntot;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (MIX) {
+      v[c] = p.velf[c * nt + i];
+      a[c] = (double)(p.frcf[c * nt + i] * (float)p.inv_mass);
+    } else {
+      v[c] = p.veld[c * nt + i];
+      a[c] = p.frcd[c * nt + i] * p.inv_mass;
+    }
+  }
+}
+
+// Stand-alone position update for every particle (first step of a call,
+// Nose-Hoover steps, and the step after a resampling). With `rescale` the
+// velocities are first centred and scaled by the replica's resampling factors.
+template <bool MIX>
+__device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bool drift) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ntot; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n) continue;
+    double v[3], a[3];
+    load_va<MIX>(p, i, v, a);
+    if (rescale) {
+      const int64_t nt = p.ntot;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (MIX) {
+          const float vf = ((float)v[c] - (float)R.vmean[c]) * (float)R.vscale;
+          p.velf[c * nt + i] = vf;
+          v[c] = vf;
+        } else {
+          v[c] = (v[c] - R.vmean[c]) * R.vscale;
+          p.veld[c * nt + i] = v[c];
+        }
+      }
+    }
+    if (drift) {
+      uint32_t type;
+      if constexpr (MIX) type = p.pq[cur][i].w; else type = 0;
+      drift_atom<MIX>(p, R, i, cur, v[0], v[1], v[2], a[0], a[1], a[2], nh ? R.xi : 0.0, type);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ forces
+
+// Sum the per-lane energies of one tile (T warps) in a fixed order and store
+// the tile's partials. Every thread of the block calls this.
+__device__ __forceinline__ void tile_partials(const KParams& p, Shared& sh, double* part, int tile, bool valid,
+                                              int T, double e[6]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e[k] = warp_sum(e[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sh.red[warp][k] = e[k];
+  }
+  __syncthreads();
+  const int gsz = 32 * T;
+  if (valid && (threadIdx.x % gsz) == 0) {
+    const int w0 = warp;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < T; ++w)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += sh.red[w0 + w][k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) part[(int64_t)tile * MD_NPART + k] = acc[k];
+  }
+  __syncthreads();
+}
+
+template <bool MIX>
+__device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs) {
+  const int T = p.T;
+  const int gsz = 32 * T;
+  const int tpb = blockDim.x / gsz;
+  const int tib = threadIdx.x / gsz;
+  const int rr = threadIdx.x - tib * gsz;
+  const int a = rr / T, s = rr - a * T;
+  const int64_t nt = p.ntot;
+  for (int base = blockIdx.x * tpb; base < p.ntiles; base += gridDim.x * tpb) {
+    const int tile = base + tib;
+    const bool valid = tile < p.ntiles;
+    double e[6] = {0, 0, 0, 0, 0, 0};
+    const RepDev* R = nullptr;
+    bool act = false;
+    int64_t i = 0;
+    if (valid) {
+      R = &p.reps[p.tile_rep[tile]];
+      act = (tile - R->tile0) * 32 + a < R->n;
+      i = (int64_t)tile * 32 + a;
+    }
+    // ---- pair loop (each of the T lanes takes every T-th list entry)
+    double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
+    uint32_t type_i = 0;
+    if (act && pairs) {
+      const int cnt = p.nnb[i];
+      const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
+      if constexpr (MIX) {
+        const uint4* __restrict__ pq = p.pq[cur];
+        const uint4 pi = pq[i];
+        type_i = pi.w;
+        const int tb = (int)pi.w * p.ntypes;
+        const float sc = R->fxs;
+        float ffx = 0.f, ffy = 0.f, ffz = 0.f, fpe = 0.f, fvir = 0.f;
+#pragma unroll 4
+        for (int k = s; k < cnt; k += T, lp += gsz) {
+          const int j = *lp;
+          const uint4 pj = pq[j];
+          const float dx = (float)(int)(pi.x - pj.x) * sc;
+          const float dy = (float)(int)(pi.y - pj.y) * sc;
+          const float dz = (float)(int)(pi.z - pj.z) * sc;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const int tt = tb + (int)pj.w;
+          const float4 c = sh.tabf[tt];
+          const float ir2 = __fdividef(1.0f, r2);
+          const float s2 = c.y * ir2;
+          const float s6 = s2 * s2 * s2;
+          const float w = c.z * s6 * (s6 - 0.5f);
+          const bool in = r2 < c.x;
+          const float fr = in ? w * ir2 : 0.0f;
+          ffx = fmaf(fr, dx, ffx);
+          ffy = fmaf(fr, dy, ffy);
+          ffz = fmaf(fr, dz, ffz);
+          fpe += in ? fmaf(c.w * s6, s6 - 1.0f, -sh.vshf[tt]) : 0.0f;
+          fvir += in ? w : 0.0f;
+        }
+        fx = ffx; fy = ffy; fz = ffz; pe = fpe; vir = fvir;
+      } else {
+        const double4_32a* __restrict__ p4 = p.p4[cur];
+        const double4_32a pi = p4[i];
+        type_i = (uint32_t)pi.w;
+        const int tb = (int)pi.w * p.ntypes;
+        const double L = R->L, hL = 0.5 * R->L;
+        for (int k = s; k < cnt; k += T, lp += gsz) {
+          const int j = *lp;
+          const double4_32a pj = p4[j];
+          double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+          if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+          if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          const int tt = tb + (int)pj.w;
+          const double4_32a c = sh.tabd[tt];
+          if (r2 < c.x) {
+            const double ir2 = 1.0 / r2;
+            const double s2 = c.y * ir2;
+            const double s6 = s2 * s2 * s2;
+            const double w = c.z * s6 * (s6 - 0.5);
+            const double fr = w * ir2;
+            fx += fr * dx; fy += fr * dy; fz += fr * dz;
+            pe += c.w * s6 * (s6 - 1.0) - sh.vshd[tt];
+            vir += w;
+          }
+        }
+      }
+    }
+    // ---- combine the T lanes of each particle (fixed xor order)
+    for (int o = T >> 1; o > 0; o >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o);
+      pe += __shfl_xor_sync(0xffffffffu, pe, o);
+      vir += __shfl_xor_sync(0xffffffffu, vir, o);
+    }
+    // ---- velocity update, stores, energies, fused drift (one lane per particle)
+    if (act && s == 0) {
+      double v[3], ao[3];
+      load_va<MIX>(p, i, v, ao);
+      const double F[3] = {fx, fy, fz};
+      double an[3];
+      if constexpr (MIX) {
+        const float im = (float)p.inv_mass, hdt = 0.5f * (float)p.dt;
+        const float xi = (float)R->xi, xia = (float)R->xi_a;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float af = (float)F[c] * im;
+          an[c] = af;
+          float vf = (float)v[c];
+          const float aof = (float)ao[c];
+          if (kick == KICK_VV) vf = fmaf(hdt, aof + af, vf);
+          else if (kick == KICK_NH) vf = vf + hdt * ((aof + af) - (xi + xia) * vf) * (1.0f - hdt * xia);
+          else if (kick == KICK_NH_EXACT) vf = (vf + hdt * (aof - xi * vf + af)) / (1.0f + hdt * xia);
+          v[c] = vf;
+          if (pairs) p.frcf[c * nt + i] = (float)F[c];
+          if (kick != KICK_NONE) p.velf[c * nt + i] = vf;
+        }
+      } else {
+        const double im = p.inv_mass, hdt = 0.5 * p.dt;
+        const double xi = R->xi, xia = R->xi_a;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double ad = F[c] * im;
+          an[c] = ad;
+          double vd = v[c];
+          if (kick == KICK_VV) vd = vd + hdt * (ao[c] + ad);
+          else if (kick == KICK_NH) vd = vd + hdt * ((ao[c] + ad) - (xi + xia) * vd) * (1.0 - hdt * xia);
+          else if (kick == KICK_NH_EXACT) vd = (vd + hdt * (ao[c] - xi * vd + ad)) / (1.0 + hdt * xia);
+          v[c] = vd;
+          if (pairs) p.frcd[c * nt + i] = F[c];
+          if (kick != KICK_NONE) p.veld[c * nt + i] = vd;
+        }
+      }
+      const double m = p.mass;
+      e[0] = 0.5 * pe;
+      e[1] = 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      e[2] = 0.5 * vir;
+      e[3] = m * v[0];
+      e[4] = m * v[1];
+      e[5] = m * v[2];
+      if (fuse) drift_atom<MIX>(p, *R, i, cur, v[0], v[1], v[2], an[0], an[1], an[2], 0.0, type_i);
+    }
+    tile_partials(p, sh, part, tile, valid, T, e);
+  }
+}
+
+// ------------------------------------------------------------------ resampling
+
+// Draw Maxwell-Boltzmann velocities (step 1 of the flow chart in Sec.
+// "Statistical temperature bath") and store per-tile sums of v and v^2.
+template <bool MIX>
+__device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nt = p.ntot;
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < p.ntiles; tile += nw) {
+    const RepDev& R = p.reps[p.tile_rep[tile]];
+    const int64_t i = tile * 32 + lane;
+    double e[4] = {0, 0, 0, 0};
+    if (i - R.off < R.n) {
+      double g[3];
+      gauss3(p.seed, draw, (uint32_t)(p.gid[i] - R.out0), g);
+      const double sd = sqrt(R.T_target * p.inv_mass);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double v = sd * g[c];
+        if constexpr (MIX) {
+          const float vf = (float)v;
+          p.velf[c * nt + i] = vf;
+          v = vf;
+        } else {
+          p.veld[c * nt + i] = v;
+        }
+        e[c] = v;
+        e[3] += v * v;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = warp_sum(e[k]);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) part[tile * MD_NPART + k] = e[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
+                                            int64_t step, bool log_now, int64_t log_idx, bool nh);
+
+// One warp per replica: fixed-order sum of the replica's tile partials, then
+// the scalar updates of the mode and, if asked, one thermo record.
+__device__ void reduce_phase(const KParams& p, const double* part, int mode, int64_t step, bool log_now,
+                             int64_t log_idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool nh = (p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT) && p.op == MD_OP_STEPS;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < p.nrep; r += nw) {
+    RepDev& R = p.reps[r];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = lane; t < R.ntiles; t += 32) {
+      const double* q = part + (int64_t)(R.tile0 + t) * MD_NPART;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += q[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
+  }
+}
+
+__device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
+                                            int64_t step, bool log_now, int64_t log_idx, bool nh) {
+  {
+    const double n = (double)R.n, X = 3.0 * n, dt = p.dt;
+    if (mode == RED_RESAMPLE) {
+      const double mx = acc[0] / n, my = acc[1] / n, mz = acc[2] / n;
+      const double S = acc[3] - n * (mx * mx + my * my + mz * mz);
+      const double sc = (S > 0.0) ? sqrt(X * R.T_target / (p.mass * S)) : 0.0;
+      R.vmean[0] = mx; R.vmean[1] = my; R.vmean[2] = mz;
+      R.vscale = sc;
+      R.ke = 0.5 * p.mass * sc * sc * S;
+      R.px = R.py = R.pz = 0.0;
+    } else {
+      if (mode == RED_FORCES || mode == RED_STEP) { R.pe = acc[0]; R.vir = acc[2]; }
+      R.ke = acc[1];
+      R.px = acc[3]; R.py = acc[4]; R.pz = acc[5];
+      if (nh) {
+        const double gnew = (2.0 * R.ke - X * R.T_target) / R.Q;
+        if (mode == RED_STEP) {
+          R.xi = R.xi + 0.5 * dt * (R.g + gnew);  // Eq. (FoxAndersen_ydottplush)
+          R.lns = R.lns_next;
+        }
+        R.g = gnew;
+        R.xi_a = R.xi + dt * R.g;                              // Eq. (Noseupdate_xiapprox)
+        R.lns_next = R.lns + R.xi * dt + 0.5 * R.g * dt * dt;  // Eq. (Noseupdate_lns)
+      }
+    }
+    if (log_now && p.thermo) {
+      ThermoDev th;
+      th.step = step;
+      th.T = 2.0 * R.ke / X;
+      th.pe_per_n = R.pe / n;
+      th.ke_per_n = R.ke / n;
+      th.etot_per_n = (R.ke + R.pe) / n;
+      th.virial = R.vir;
+      th.h_nh = R.ke + R.pe + (nh ? 0.5 * R.Q * R.xi * R.xi + X * R.T_target * R.lns : 0.0);
+      th.xi = nh ? R.xi : 0.0;
+      p.thermo[log_idx * p.nrep + r] = th;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ rebuild
+
+template <bool MIX>
+__device__ __forceinline__ void cell_of_pos(const KParams& p, const RepDev& R, int64_t i, int cur, int& cx, int& cy,
+                                            int& cz) {
+  const int nc = R.nc;
+  if constexpr (MIX) {
+    const uint4 q = p.pq[cur][i];
+    cx = (int)(((uint64_t)q.x * (uint64_t)nc) >> 32);
+    cy = (int)(((uint64_t)q.y * (uint64_t)nc) >> 32);
+    cz = (int)(((uint64_t)q.z * (uint64_t)nc) >> 32);
+  } else {
+    const double4_32a x = p.p4[cur][i];
+    const double s = (double)nc * R.invL;
+    cx = min(max((int)(x.x * s), 0), nc - 1);
+    cy = min(max((int)(x.y * s), 0), nc - 1);
+    cz = min(max((int)(x.z * s), 0), nc - 1);
+  }
+}
+
+// Block-wide exclusive scan of one int per thread.
+__device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh.scan[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nwarp ? sh.scan[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nwarp) sh.scan[lane] = w;
+  }
+  __syncthreads();
+  const int before = (warp > 0 ? sh.scan[warp - 1] : 0) + x - v;
+  *total = sh.scan[nwarp - 1];
+  __syncthreads();
+  return before;
+}
+
+// Cell sort + Verlet list build for every replica whose want_rebuild is set.
+// Returns false after a barrier timeout. *fl receives the last snapshot.
+template <bool MIX>
+__device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nt = p.ntot;
+  // B1: cell index and count per cell; owners copy want -> doing
+  for (int64_t r = gtid; r < p.nrep; r += stride) p.reps[r].doing_rebuild = p.reps[r].want_rebuild;
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.want_rebuild || R.nc == 0) continue;
+    int cx, cy, cz;
+    cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
+    const int c = (cz * R.nc + cy) * R.nc + cx;
+    p.cellof[i] = c;
+    atomicAdd(&p.ccount[R.cell0 + c], 1);
+  }
+  int f = grid_sync(p, sh, 101);
+  if (f < 0) return false;
+  // B2: per-replica exclusive scan of the cell counts (one CTA per replica)
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAnd(&p.ctl->pending, ~MD_FLAG_REBUILD);
+  for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
+    RepDev& R = p.reps[r];
+    if (!R.doing_rebuild) continue;
+    if (threadIdx.x == 0) {
+      R.want_rebuild = 0;
+      R.rebuilds += 1;
+      R.list_entries = 0;
+    }
+    if (R.nc == 0) continue;
+    const int ncell = R.nc * R.nc * R.nc;
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    const int b0 = min((int)threadIdx.x * per, ncell), b1 = min(b0 + per, ncell);
+    int sum = 0;
+    for (int c = b0; c < b1; ++c) sum += p.ccount[R.cell0 + c];
+    int total;
+    const int pre = block_exclusive_scan(sh, sum, &total);
+    int run = (int)R.off + pre;
+    for (int c = b0; c < b1; ++c) {
+      const int k = p.ccount[R.cell0 + c];
+      p.cstart[R.cs0 + c] = run;
+      p.ccursor[R.cell0 + c] = run;
+      p.ccount[R.cell0 + c] = 0;
+      run += k;
+    }
+    if (threadIdx.x == 0) p.cstart[R.cs0 + ncell] = (int)(R.off + R.n);
+  }
+  f = grid_sync(p, sh, 102);
+  if (f < 0) return false;
+  // B3: scatter slot indices into their cells (order inside a cell arbitrary)
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
+    const int slot = atomicAdd(&p.ccursor[R.cell0 + p.cellof[i]], 1);
+    p.scat[slot] = (int)i;
+  }
+  f = grid_sync(p, sh, 103);
+  if (f < 0) return false;
+  // B4: rank inside the cell by caller index (deterministic order) and move
+  // every per-particle array to its new slot in the scratch copy
+  for (int64_t k = gtid; k < nt; k += stride) {
+    const RepDev& R = p.reps[p.tile_rep[k >> 5]];
+    if (k - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
+    const int o = p.scat[k];
+    const int c = p.cellof[o];
+    const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
+    const int my = p.gid[o];
+    int rank = 0;
+    for (int q = lo; q < hi; ++q) rank += (p.gid[p.scat[q]] < my);
+    const int64_t d = lo + rank;
+    if constexpr (MIX) {
+      for (int cc = 0; cc < 3; ++cc) {
+        p.t_pfx[cc * nt + d] = p.pfx[cc * nt + o];
+        ((float*)p.t_vel)[cc * nt + d] = p.velf[cc * nt + o];
+        ((float*)p.t_frc)[cc * nt + d] = p.frcf[cc * nt + o];
+        p.t_img[cc * nt + d] = p.img[cc * nt + o];
+      }
+    } else {
+      p.t_p4[d] = p.p4[cur][o];
+      for (int cc = 0; cc < 3; ++cc) {
+        ((double*)p.t_vel)[cc * nt + d] = p.veld[cc * nt + o];
+        ((double*)p.t_frc)[cc * nt + d] = p.frcd[cc * nt + o];
+        p.t_img[cc * nt + d] = p.img[cc * nt + o];
+      }
+    }
+    p.t_gid[d] = p.gid[o];
+    p.t_typ[d] = p.typ[o];
+  }
+  f = grid_sync(p, sh, 104);
+  if (f < 0) return false;
+  // B5: copy back, refresh the gather copy
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
+    if constexpr (MIX) {
+      uint32_t hi[3];
+      for (int cc = 0; cc < 3; ++cc) {
+        const uint64_t u = p.t_pfx[cc * nt + i];
+        p.pfx[cc * nt + i] = u;
+        hi[cc] = (uint32_t)(u >> 32);
+        p.velf[cc * nt + i] = ((const float*)p.t_vel)[cc * nt + i];
+        p.frcf[cc * nt + i] = ((const float*)p.t_frc)[cc * nt + i];
+        p.img[cc * nt + i] = p.t_img[cc * nt + i];
+      }
+      p.pq[cur][i] = make_uint4(hi[0], hi[1], hi[2], p.t_typ[i]);
+    } else {
+      p.p4[cur][i] = p.t_p4[i];
+      for (int cc = 0; cc < 3; ++cc) {
+        p.veld[cc * nt + i] = ((const double*)p.t_vel)[cc * nt + i];
+        p.frcd[cc * nt + i] = ((const double*)p.t_frc)[cc * nt + i];
+        p.img[cc * nt + i] = p.t_img[cc * nt + i];
+      }
+    }
+    p.gid[i] = p.t_gid[i];
+    p.typ[i] = p.t_typ[i];
+  }
+  f = grid_sync(p, sh, 105);
+  if (f < 0) return false;
+  // B6: Verlet list over the 27 neighbouring cells (or all particles of a
+  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin.
+  const int T = p.T, gsz = 32 * T;
+  const int cap = p.maxrows * T;
+  for (int64_t i = gtid; i < nt; i += stride) {
+    RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.doing_rebuild) continue;
+    const int a = (int)(i & 31);
+    int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + a * T;
+    int k = 0;
+    int cx = 0, cy = 0, cz = 0;
+    const int nc = R.nc;
+    if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
+    const int ncell_iter = nc > 0 ? 27 : 1;
+    if constexpr (MIX) {
+      const uint4 pi = p.pq[cur][i];
+      const int tb = (int)pi.w * p.ntypes;
+      const float sc = R.fxs;
+      for (int cc = 0; cc < ncell_iter; ++cc) {
+        int lo, hi;
+        if (nc > 0) {
+          const int ox = cc % 3 - 1, oy = (cc / 3) % 3 - 1, oz = cc / 9 - 1;
+          const int c = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+          lo = p.cstart[R.cs0 + c];
+          hi = p.cstart[R.cs0 + c + 1];
+        } else {
+          lo = (int)R.off;
+          hi = (int)(R.off + R.n);
+        }
+        for (int j = lo; j < hi; ++j) {
+          if (j == i) continue;
+          const uint4 pj = p.pq[cur][j];
+          const float dx = (float)(int)(pi.x - pj.x) * sc;
+          const float dy = (float)(int)(pi.y - pj.y) * sc;
+          const float dz = (float)(int)(pi.z - pj.z) * sc;
+          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
+            if (k < cap) lb[(k / T) * gsz + (k % T)] = j;
+            ++k;
+          }
+        }
+      }
+      p.xbq[i] = pi;
+    } else {
+      const double4_32a pi = p.p4[cur][i];
+      const int tb = (int)pi.w * p.ntypes;
+      const double L = R.L, hL = 0.5 * R.L;
+      for (int cc = 0; cc < ncell_iter; ++cc) {
+        int lo, hi;
+        if (nc > 0) {
+          const int ox = cc % 3 - 1, oy = (cc / 3) % 3 - 1, oz = cc / 9 - 1;
+          const int c = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+          lo = p.cstart[R.cs0 + c];
+          hi = p.cstart[R.cs0 + c + 1];
+        } else {
+          lo = (int)R.off;
+          hi = (int)(R.off + R.n);
+        }
+        for (int j = lo; j < hi; ++j) {
+          if (j == i) continue;
+          const double4_32a pj = p.p4[cur][j];
+          double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+          if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+          if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+          if (dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
+            if (k < cap) lb[(k / T) * gsz + (k % T)] = j;
+            ++k;
+          }
+        }
+      }
+      p.xbd[i] = pi;
+    }
+    if (k > cap) raise_flag(p, MD_FLAG_OVERFLOW);
+    p.nnb[i] = min(k, cap);
+    atomicAdd((unsigned long long*)&R.list_entries, (unsigned long long)min(k, cap));
+  }
+  f = grid_sync(p, sh, 106);
+  if (f < 0) return false;
+  *fl = f;
+  return true;
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <bool MIX>
+__global__ void __launch_bounds__(512) md_persistent(KParams p) {
+  __shared__ Shared sh;
+  const int nt2 = p.ntypes * p.ntypes;
+  for (int t = threadIdx.x; t < nt2; t += blockDim.x) {
+    sh.tabf[t] = make_float4(p.tab_f[t][0], p.tab_f[t][1], p.tab_f[t][2], p.tab_f[t][3]);
+    sh.vshf[t] = p.vsh_f[t];
+    sh.rl2f[t] = p.rl2_f[t];
+    sh.tabd[t] = make_double4_32a(p.tab_d[t][0], p.tab_d[t][1], p.tab_d[t][2], p.tab_d[t][3]);
+    sh.vshd[t] = p.vsh_d[t];
+    sh.rl2d[t] = p.rl2_d[t];
+  }
+  CtlDev* C = p.ctl;
+  int cur = C->cur;
+  const int drifted = C->drifted;
+  const int fvalid = C->forces_valid;
+  const int64_t step0 = C->step;
+  int fl = grid_sync(p, sh, 1);
+  if (fl < 0) return;
+  const bool nh = p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT;
+  const int kick = p.kind == MD_KIND_NH ? KICK_NH : (p.kind == MD_KIND_NH_EXACT ? KICK_NH_EXACT : KICK_VV);
+  int64_t done = 0;
+  bool now_drifted = drifted != 0;
+
+  // record where this launch left the state: the gather-buffer parity, the
+  // global step, whether positions are one drift ahead of velocities/forces,
+  // and whether the stored forces belong to the stored positions
+  auto finish = [&](bool is_drifted, int forces_valid) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C->cur = cur;
+      C->step = step0 + done;
+      C->steps_done = done;
+      C->drifted = is_drifted ? 1 : 0;
+      C->forces_valid = forces_valid;
+    }
+  };
+
+  if (!drifted) {
+    if (fl & MD_FLAG_REBUILD) {
+      if (!rebuild<MIX>(p, sh, cur, &fl)) return;
+      if (fl & MD_FLAG_OVERFLOW) { finish(false, fvalid); return; }
+    }
+    if (p.op == MD_OP_REBUILD) { finish(false, fvalid); return; }
+    if (p.op == MD_OP_INITVEL) {
+      // Maxwell-Boltzmann start: draw 0 at each replica's bath temperature,
+      // then centre and rescale (steps 1-4 of Sec. "Statistical temperature bath")
+      resample_draw_phase<MIX>(p, 0, p.part[0]);
+      if ((fl = grid_sync(p, sh, 2)) < 0) return;
+      reduce_phase(p, p.part[0], RED_RESAMPLE, step0, false, 0);
+      if ((fl = grid_sync(p, sh, 3)) < 0) return;
+      drift_phase<MIX>(p, cur, false, true, false);
+      finish(false, fvalid);
+      return;
+    }
+    const bool pairs = !fvalid || p.op == MD_OP_FORCES;
+    force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs);
+    if ((fl = grid_sync(p, sh, 4)) < 0) return;
+    reduce_phase(p, p.part[0], pairs ? RED_FORCES : RED_KE, step0, false, 0);
+    if ((fl = grid_sync(p, sh, 5)) < 0) return;
+    if (p.op == MD_OP_FORCES || p.nsteps == 0) { finish(false, 1); return; }
+    drift_phase<MIX>(p, cur, nh, false, true);
+    cur ^= 1;
+    now_drifted = true;
+    if ((fl = grid_sync(p, sh, 6)) < 0) return;
+  }
+  for (int64_t s = 0; s < p.nsteps; ++s) {
+    if (fl & MD_FLAG_UNSTABLE) break;
+    if (fl & MD_FLAG_REBUILD) {
+      if (!rebuild<MIX>(p, sh, cur, &fl)) return;
+      if (fl & MD_FLAG_OVERFLOW) { finish(true, 1); return; }
+    }
+    const int64_t step = step0 + s + 1;
+    const bool last = s == p.nsteps - 1;
+    const bool rs = p.kind == MD_KIND_RESAMPLE && (step % p.nstep_boltz == 0);
+    const bool fuse = !nh && !rs && !last;
+    double* part = p.part[step & 1];
+    force_phase<MIX>(p, sh, cur, kick, fuse, part, true);
+    if ((fl = grid_sync(p, sh, 10)) < 0) return;
+    if (fuse) cur ^= 1;
+    now_drifted = fuse;
+    const int64_t li = p.log_step0 + s + 1;
+    const bool log_now = p.log_every > 0 && (li % p.log_every) == 0 && (li / p.log_every - 1) < p.log_cap;
+    const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
+    if (log_now || nh || last || rs) reduce_phase(p, part, RED_STEP, step, log_now && !rs, lidx);
+    if (nh) {
+      if ((fl = grid_sync(p, sh, 11)) < 0) return;
+      if (!last) {
+        drift_phase<MIX>(p, cur, true, false, true);
+        cur ^= 1;
+        now_drifted = true;
+        if ((fl = grid_sync(p, sh, 12)) < 0) return;
+      }
+    } else if (rs) {
+      if ((fl = grid_sync(p, sh, 13)) < 0) return;
+      double* part2 = p.part[(step & 1) ^ 1];
+      resample_draw_phase<MIX>(p, (uint64_t)(step / p.nstep_boltz), part2);
+      if ((fl = grid_sync(p, sh, 14)) < 0) return;
+      reduce_phase(p, part2, RED_RESAMPLE, step, log_now, lidx);
+      if ((fl = grid_sync(p, sh, 15)) < 0) return;
+      drift_phase<MIX>(p, cur, false, true, !last);
+      if (!last) { cur ^= 1; now_drifted = true; }
+      if ((fl = grid_sync(p, sh, 16)) < 0) return;
+    }
+    done = s + 1;
+  }
+  finish(now_drifted && done < p.nsteps, 1);
+}
+
+}  // namespace kamd
+
+cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s) {
+  void* args[] = {(void*)&p};
+  if (mixed)
+    return cudaLaunchCooperativeKernel((const void*)kamd::md_persistent<true>, dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)kamd::md_persistent<false>, dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t md_occupancy(bool mixed, int block, int* blocks_per_sm) {
+  if (mixed)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kamd::md_persistent<true>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kamd::md_persistent<false>, block, 0);
+}

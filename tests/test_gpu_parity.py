@@ -1,0 +1,287 @@
+"""GPU path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+Tolerances (force metric = max_i |dF_i| / F_rms and ||dF||_2 / ||F||_2; energy
+metric = |dE| / (|KE| + |PE|), the scale of the terms that make up E, because
+E_tot itself can sit near zero):
+  FP64 path   forces <= 1e-12, energies <= 1e-12 (single evaluation), 1e-10 over a trajectory
+  mixed path  forces <= 1e-5, energies per step <= 1e-6
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_07089_gb300 import kamd
+from paper_2001_07089_gb300 import workloads as wl
+from tests.helpers import force_errors, ka_params, melted, min_image_diff
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {"fp64": 1e-12, "mixed": 1e-5}
+TOL_E = {"fp64": 1e-12, "mixed": 1e-6}
+PRECS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kamd.load()
+
+
+def make_system(n, L, types, prec, skin=0.3, tpa=None):
+    s = kamd.System(n, L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, skin, prec)
+    if tpa is not None:
+        s.set_tuning(threads_per_atom=tpa)
+    return s
+
+
+def check_forces(f_gpu, f_ref, prec):
+    emax, e2 = force_errors(f_gpu, f_ref)
+    assert emax <= TOL_F[prec] and e2 <= TOL_F[prec], (emax, e2)
+
+
+# ------------------------------------------------------------------ forces
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,seed", [(250, 21), (1000, 22), (4000, 23)])
+def test_forces_match_oracle_melted(prec, n, seed):
+    pos, vel, types, L = melted(n, seed, nsteps=200)
+    f_ref, v_ref, w_ref = oracle.forces(pos, types, ka_params(), L)
+    with make_system(n, L, types, prec) as s:
+        s.set_state(pos, vel)
+        f, pe, vir = s.forces()
+    check_forces(f, f_ref, prec)
+    assert abs(pe[0] - v_ref) <= TOL_E[prec] * abs(v_ref)
+    assert abs(vir[0] - w_ref) <= TOL_E[prec] * abs(w_ref) * 10
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("tpa", [1, 2, 4, 8])
+def test_forces_every_lane_split(prec, tpa):
+    pos, vel, types, L = melted(1000, 24, nsteps=200)
+    f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
+    with make_system(1000, L, types, prec, tpa=tpa) as s:
+        s.set_state(pos, vel)
+        f, pe, _ = s.forces()
+    check_forces(f, f_ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_32k_jittered_lattice(prec):
+    n = 32000
+    L = wl.box_length(n)
+    types = wl.ka_types(n, 25).astype(np.int32)
+    pos, vel = oracle.init_lattice(n, L, 2.0, seed=25, jitter=0.2)
+    f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
+    with make_system(n, L, types, prec) as s:
+        s.set_state(pos, vel)
+        f, pe, _ = s.forces()
+    check_forces(f, f_ref, prec)
+    assert abs(pe[0] - v_ref) <= TOL_E[prec] * abs(v_ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiny_systems_and_ragged_tiles(prec):
+    """N = 2 and 3 in a large box, and N = 33 (one full tile plus one particle)."""
+    L = 10.0
+    for pos, types in [
+        (np.array([[1.0, 1.0, 1.0], [2.05, 1.2, 0.9]]), np.array([0, 1])),
+        (np.array([[1.0, 1.0, 1.0], [2.05, 1.2, 0.9], [9.6, 1.1, 1.3]]), np.array([0, 1, 0])),
+    ]:
+        f_ref, v_ref, _ = oracle.forces(pos, types.astype(np.int32), ka_params(), L)
+        with make_system(len(pos), L, types, prec) as s:
+            s.set_state(pos, np.zeros_like(pos))
+            f, pe, _ = s.forces()
+        check_forces(f, f_ref, prec)
+        assert abs(pe[0] - v_ref) <= TOL_E[prec] * abs(v_ref)
+    n = 33
+    L = wl.box_length(n, 0.2)
+    types = wl.ka_types(n, 26).astype(np.int32)
+    pos = wl.uniform_positions(n, L, 26)
+    f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
+    with make_system(n, L, types, prec) as s:
+        s.set_state(pos, np.zeros_like(pos))
+        f, pe, _ = s.forces()
+    check_forces(f, f_ref, prec)
+
+
+# ------------------------------------------------------------------ dynamics
+
+def thermo_rel(gpu_log, ref_thermo, field_gpu, col, n=1):
+    """Largest per-step error of one thermo field, relative to |KE| + |PE| (times n for totals)."""
+    a = gpu_log[field_gpu][:, 0]
+    b = ref_thermo[:, col]
+    scale = n * (np.abs(ref_thermo[:, 2]) + np.abs(ref_thermo[:, 3]))
+    return np.max(np.abs(a - b) / scale)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nve_100_steps_energies(prec):
+    pos, vel, types, L = melted(1000, 31, nsteps=200)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 100, log_every=1)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nve(0.005, 100, log_every=1)
+        p, v, img = s.get_state()
+    assert list(log["step"][:, 0]) == list(range(1, 101))
+    tol = 1e-10 if prec == "fp64" else TOL_E["mixed"]
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= tol
+    assert thermo_rel(log, ref["thermo"], "pe_per_n", 2) <= tol
+    assert thermo_rel(log, ref["thermo"], "ke_per_n", 3) <= tol
+    d = np.abs(min_image_diff(p, ref["pos"], L))
+    assert d.max() < (1e-9 if prec == "fp64" else 1e-3)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", [kamd.MD_NVT_NOSE_HOOVER, kamd.MD_NVT_NOSE_HOOVER_EXACT])
+def test_nose_hoover_100_steps(prec, kind):
+    pos, vel, types, L = melted(1000, 32, nsteps=200)
+    T, tau = 0.8, 0.5
+    n = 1000
+    okind = oracle.NOSE_HOOVER if kind == kamd.MD_NVT_NOSE_HOOVER else oracle.NOSE_HOOVER_EXACT
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 100, kind=okind, T_target=T, Q=3 * n * T * tau * tau,
+                     log_every=1)
+    with make_system(n, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nvt(0.005, 100, T, kind=kind, param=tau, log_every=1)
+    tol = 1e-10 if prec == "fp64" else TOL_E["mixed"]
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= tol
+    assert thermo_rel(log, ref["thermo"], "h_nh", 6, n=n) <= tol
+    assert thermo_rel(log, ref["thermo"], "T", 1) <= (1e-10 if prec == "fp64" else 1e-5)
+    xi_g, xi_r = log["xi"][:, 0], ref["thermo"][:, 7]
+    assert np.max(np.abs(xi_g - xi_r)) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(xi_r))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_resample_bath(prec):
+    pos, vel, types, L = melted(1000, 33, nsteps=100)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 40, kind=oracle.RESAMPLE, T_target=0.5, nstep_boltz=10,
+                     seed=77, log_every=1)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nvt(0.005, 40, 0.5, kind=kamd.MD_NVT_RESAMPLE, param=10, seed=77, log_every=1)
+        p, v, _ = s.get_state()
+    for k in (9, 19, 29, 39):
+        assert abs(log["T"][k, 0] - 0.5) < 1e-12
+    tol = 1e-10 if prec == "fp64" else TOL_E["mixed"]
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= tol
+    # the step-40 velocities are a fresh draw: identical up to rounding
+    assert np.max(np.abs(v - ref["vel"])) < (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_init_lattice_matches_oracle(prec):
+    for n in (1000, 4000):
+        L = wl.box_length(n)
+        types = wl.ka_types(n, 41)
+        pos_r, vel_r = oracle.init_lattice(n, L, 2.0, seed=41, jitter=0.05)
+        with make_system(n, L, types, prec) as s:
+            s.init_lattice(2.0, 0.05, 41)
+            p, v, _ = s.get_state()
+        assert np.max(np.abs(min_image_diff(p, pos_r, L))) < (1e-12 if prec == "fp64" else 1e-8)
+        assert np.max(np.abs(v - vel_r)) < (1e-12 if prec == "fp64" else 1e-6)
+        assert np.sum(v * v) / (3 * n) == pytest.approx(2.0, rel=1e-12 if prec == "fp64" else 1e-6)
+
+
+# ------------------------------------------------------------------ structure
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_deterministic_bitwise(prec):
+    pos, vel, types, L = melted(1000, 51, nsteps=100)
+    out = []
+    for _ in range(2):
+        with make_system(1000, L, types, prec) as s:
+            s.set_state(pos, vel)
+            log = s.step_nvt(0.005, 60, 1.0, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5, log_every=10)
+            out.append((s.get_state(), log))
+    (a, la), (b, lb) = out
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(la, lb)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_replicas_equal_standalone_runs(prec):
+    ns = [250, 1000, 500, 2000]
+    Ts = [0.6, 1.2, 0.9, 2.0]
+    cfg = [melted(n, 60 + k, nsteps=50) for k, n in enumerate(ns)]
+    Ls = [c[3] for c in cfg]
+    types = np.concatenate([c[2] for c in cfg])
+    with kamd.System(ns, Ls, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, 1.0, 0.3, prec) as b:
+        b.set_state(np.concatenate([c[0] for c in cfg]), np.concatenate([c[1] for c in cfg]))
+        blog = b.step_nvt(0.005, 80, Ts, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5, log_every=20)
+        bp, bv, bi = b.get_state()
+    off = 0
+    for k, n in enumerate(ns):
+        with make_system(n, Ls[k], cfg[k][2], prec) as s:
+            s.set_state(cfg[k][0], cfg[k][1])
+            log = s.step_nvt(0.005, 80, Ts[k], kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5, log_every=20)
+            p, v, i = s.get_state()
+        assert np.array_equal(p, bp[off:off + n]) and np.array_equal(v, bv[off:off + n])
+        assert np.array_equal(log[:, 0], blog[:, k])
+        off += n
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rebuilds_keep_parity_over_long_nve(prec):
+    """400 NVE steps at T=2 cross many list rebuilds; the energy trace stays on the oracle's."""
+    pos, vel, types, L = melted(1000, 71, nsteps=100)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 400, log_every=20)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nve(0.005, 400, log_every=20)
+        info = s.info()
+    assert info["rebuilds"] >= 5
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= (1e-9 if prec == "fp64" else 1e-5)
+
+
+def test_sampled_forces_one_million():
+    """N = 10^6 mixed: 200 sampled particles against O(N) oracle sums."""
+    n = 1_000_000
+    L = wl.box_length(n)
+    types = wl.ka_types(n, 81)
+    with make_system(n, L, types, "mixed") as s:
+        s.init_lattice(0.5, 0.05, 81)
+        s.step_nvt(0.005, 20, 0.5, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5)
+        f, pe, _ = s.forces()
+        p, _, _ = s.get_state()
+    rng = np.random.default_rng(81)
+    idx = rng.choice(n, size=200, replace=False)
+    t32 = types.astype(np.int32)
+    ref = np.array([oracle.force_on(p, t32, ka_params(), L, i)[0] for i in idx])
+    frms = np.sqrt(np.mean(np.sum(f * f, axis=1)))
+    err = np.linalg.norm(f[idx] - ref, axis=1) / frms
+    assert err.max() <= TOL_F["mixed"], err.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rdf_and_msd_match_oracle(prec):
+    pos, vel, types, L = melted(1000, 91, nsteps=100)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        s.step_nve(0.005, 100)
+        g = s.rdf(0.05, 80, reset=True)
+        p, v, img = s.get_state()
+        msd = s.msd()
+    g_ref = oracle.rdf(p, types, L, 0.05, 80)
+    if prec == "fp64":
+        assert np.allclose(g, g_ref, rtol=1e-12, atol=1e-12)
+    else:
+        # fixed-point distances may move a pair across a bin edge: compare totals and shape
+        assert np.max(np.abs(g - g_ref)) < 0.05 * np.max(g_ref)
+    m_ref = oracle.msd(p, img, pos, types, 2, L)
+    assert np.allclose(msd, m_ref, rtol=1e-9 if prec == "fp64" else 1e-5)
+
+
+def test_count_pairs_matches_oracle():
+    pos, vel, types, L = melted(1000, 92, nsteps=100)
+    with make_system(1000, L, types, "fp64") as s:
+        s.set_state(pos, vel)
+        c = s.count_pairs()
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= L * np.rint(d / L)
+    r2 = np.sum(d * d, axis=2)
+    rc2 = (wl.KA_RC ** 2)[types[:, None], types[None, :]]
+    ref = (np.sum(r2 < rc2) - len(pos)) // 2
+    assert c == ref
