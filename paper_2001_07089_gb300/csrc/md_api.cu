@@ -133,7 +133,7 @@ void dfree(T*& p) {
 __global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const RepDev* reps, const int32_t* rep_of,
                             const uint8_t* typ_caller, const double* pos, const double* vel, int cur, uint64_t* pfx,
                             uint4* pq, float* velf, float* frcf, uint4* xbq, double4_32a* p4, double* veld,
-                            double* frcd, double4_32a* xbd, int32_t* gid, uint8_t* typ, int32_t* img, int32_t* nnb) {
+                            double* frcd, double4_32a* xbd, int32_t* gid, uint8_t* typ, int32_t* img) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_total) return;
   const RepDev& R = reps[rep_of[g]];
@@ -163,7 +163,6 @@ __global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const Rep
   for (int c = 0; c < 3; ++c) img[c * ntot + i] = 0;
   gid[i] = (int32_t)g;
   typ[i] = (uint8_t)t;
-  nnb[i] = 0;
 }
 
 // Simple-cubic lattice with jitter (Sec. "Initialization of positions").
@@ -363,27 +362,38 @@ __global__ void k_count_pairs(bool mixed, int64_t ntot, int T, int maxrows, int 
   const RepDev& R = reps[tile_rep[i >> 5]];
   if (i - R.off >= R.n) return;
   const int gsz = 32 * T;
-  const int32_t* lb = nbr + (i >> 5) * (int64_t)maxrows * gsz + (i & 31) * T;
   unsigned long long c = 0;
-  const int cnt = nnb[i];
-  for (int k = 0; k < cnt; ++k) {
-    const int j = lb[(k / T) * gsz + (k % T)];
-    if (mixed) {
-      const uint4 a = pq[i], b = pq[j];
-      const float dx = (float)(int)(a.x - b.x) * R.fxs, dy = (float)(int)(a.y - b.y) * R.fxs,
-                  dz = (float)(int)(a.z - b.z) * R.fxs;
-      c += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rc2f[a.w * ntypes + b.w];
-    } else {
-      const double4_32a a = p4[i], b = p4[j];
-      double d[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
-      for (int q = 0; q < 3; ++q) {
-        if (d[q] > 0.5 * R.L) d[q] -= R.L;
-        else if (d[q] < -0.5 * R.L) d[q] += R.L;
+  for (int s = 0; s < T; ++s) {
+    const int32_t* lb = nbr + (i >> 5) * (int64_t)maxrows * gsz + (i & 31) * T + s;
+    const int cnt = nnb[i * T + s];
+    for (int q = 0; q < cnt; ++q) {
+      const int j = lb[(int64_t)q * gsz];
+      if (mixed) {
+        const uint4 a = pq[i], b = pq[j];
+        const float dx = (float)(int)(a.x - b.x) * R.fxs, dy = (float)(int)(a.y - b.y) * R.fxs,
+                    dz = (float)(int)(a.z - b.z) * R.fxs;
+        c += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rc2f[a.w * ntypes + b.w];
+      } else {
+        const double4_32a a = p4[i], b = p4[j];
+        double d[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
+        for (int k = 0; k < 3; ++k) {
+          if (d[k] > 0.5 * R.L) d[k] -= R.L;
+          else if (d[k] < -0.5 * R.L) d[k] += R.L;
+        }
+        c += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2d[(int)a.w * ntypes + (int)b.w];
       }
-      c += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2d[(int)a.w * ntypes + (int)b.w];
     }
   }
   if (c) atomicAdd(out, c);
+}
+
+// Sum of n non-negative ints (warp sums, one atomic per warp).
+__global__ void k_sum_i32(int64_t n, const int32_t* v, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    acc += (unsigned long long)v[k];
+  acc = kamd::warp_sum(acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
 int blocks_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
@@ -514,6 +524,9 @@ KParams make_params(const md_system* s) {
   p.mass = s->mass;
   p.inv_mass = 1.0 / s->mass;
   p.skin_half2 = 0.25 * s->tun.skin * s->tun.skin;
+  p.massf = (float)s->mass;
+  p.inv_massf = (float)(1.0 / s->mass);
+  p.skin_half2f = (float)p.skin_half2;
   p.timeout_ns = s->timeout_ns;
   p.reps = s->d_reps;
   p.tile_rep = s->d_tile_rep;
@@ -567,6 +580,7 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
     p.op = op;
     p.kind = kind;
     p.dt = dt;
+    p.dtf = (float)dt;
     p.nsteps = nsteps - done;
     p.nstep_boltz = nstep_boltz;
     p.seed = seed;
@@ -651,8 +665,9 @@ md_status set_state_impl(md_system* s, const double* pos, const double* vel, int
   k_set_state<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(
       s->mixed, s->n_total, s->ntot, s->d_reps, s->d_rep_of_caller, s->d_typ_caller, dpos, dvel, 0, s->d_pfx,
       s->d_pq[0], s->d_velf, s->d_frcf, s->d_xbq, s->d_p4[0], s->d_veld, s->d_frcd, s->d_xbd, s->d_gid, s->d_typ,
-      s->d_img, s->d_nnb);
+      s->d_img);
   CK(cudaGetLastError());
+  CK(cudaMemsetAsync(s->d_nnb, 0, sizeof(int32_t) * 8 * (size_t)s->ntot, s->stream));
   return after_new_state(s);
 }
 
@@ -763,6 +778,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
     R.Lf = (float)L_per[r];
     R.fxs = (float)(L_per[r] / 4294967296.0);
     R.fx64f = (float)R.fx64;
+    R.fx32f = (float)(4294967296.0 / L_per[r]);
     s->reps[r] = R;
     s->out0.push_back(o0);
     for (int t = 0; t < R.ntiles; ++t) tile_rep.push_back(r);
@@ -819,7 +835,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   AL(s->d_timg, 3 * nt);
   AL(s->d_cellof, nt);
   AL(s->d_scat, nt);
-  AL(s->d_nnb, nt);
+  AL(s->d_nnb, 8 * nt);
   AL(s->d_part[0], (size_t)s->ntiles * MD_NPART);
   AL(s->d_part[1], (size_t)s->ntiles * MD_NPART);
   AL(s->d_typ_caller, (size_t)ntotal);
@@ -1148,9 +1164,16 @@ md_status md_get_info(md_system* s, md_info* info) {
   info->steps_done = s->ctl.step;
   for (const auto& R : s->reps) {
     info->rebuilds += R.rebuilds;
-    info->list_entries += R.list_entries;
     info->all_pairs_replicas += R.nc == 0;
   }
+  CK(cudaMemsetAsync(s->d_count, 0, 8, s->stream));
+  k_sum_i32<<<std::max(1, std::min(1024, blocks_for(s->ntot * s->tun.threads_per_atom, 256))), 256, 0, s->stream>>>(
+      s->ntot * s->tun.threads_per_atom, s->d_nnb, s->d_count);
+  CK(cudaGetLastError());
+  unsigned long long entries = 0;
+  CK(cudaMemcpyAsync(&entries, s->d_count, 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  info->list_entries = (int64_t)entries;
   info->list_capacity = (int64_t)s->maxrows * s->tun.threads_per_atom;
   info->device_bytes = (int64_t)s->bytes;
   info->precision = s->mixed ? MD_PREC_MIXED : MD_PREC_FP64;

@@ -12,9 +12,10 @@
 //   xbq   uint4 [ntot] (position at the   xbd  double4_32a [ntot]
 //         last list build, hi32)
 //   gid i32 [ntot] caller index; typ u8 [ntot]; img i32 [3][ntot] image counters
-//   nbr i32 [ntiles][maxrows][32*T]: entry k of particle a of a tile sits at
-//       row k/T, column a*T + k%T, so the T lanes that share a particle read
-//       consecutive words and a warp reads 128 contiguous bytes per row.
+//   nbr i32 [ntiles][maxrows][32*T]: lane s of particle a of a tile owns
+//       column a*T + s; its q-th neighbour sits in row q. nnb i32 [ntot*T]
+//       holds each lane's count. The T lanes of a particle read consecutive
+//       words, so a warp reads 128 contiguous bytes per row.
 //   cells: ccount/ccursor [ncells], cstart [ncells + nrep], cellof/scat [ntot]
 //
 // Fixed-point positions: u = x/L * 2^64 (mod 2^64). Wrapping into the box is
@@ -51,14 +52,17 @@ struct RepDev {
   double fx64;      // 2^64 / L
   float Lf, fxs;    // L, L / 2^32
   float fx64f;      // 2^64 / L
+  float fx32f;      // 2^32 / L
   float cellw;      // L / nc
   // bath
   double T_target, Q;
   double xi, g, lns, lns_next, xi_a;
+  float xif, xiaf;  // FP32 copies of xi and xi_a for the mixed path
   // last reductions
   double pe, ke, vir, px, py, pz;
   // resampling
   double vmean[3], vscale;
+  float vmeanf[3], vscalef;
   int32_t want_rebuild, doing_rebuild;
   int64_t rebuilds;
   int64_t list_entries;
@@ -101,6 +105,7 @@ struct KParams {
   double rl2_d[MD_MAXTYPES * MD_MAXTYPES];
   double mass, inv_mass;
   double skin_half2;   // (skin/2)^2
+  float massf, inv_massf, skin_half2f, dtf;
   // operation
   int op;
   int kind;
@@ -146,7 +151,7 @@ struct KParams {
   int32_t* nbr;
   int32_t* nnb;
   // reductions
-  double* part[2];     // [ntiles][MD_NPART]
+  double* part[2];     // [ntiles][MD_NPART]: doubles (FP64 path) or float (hi, lo) pairs (mixed path)
 };
 
 // Host-side launchers (md_kernel.cu).

@@ -26,6 +26,10 @@
 #include "md_device.cuh"
 #include "md_internal.cuh"
 
+#ifndef KAMD_MIN_BLOCKS
+#define KAMD_MIN_BLOCKS 2
+#endif
+
 namespace kamd {
 
 enum { KICK_NONE = 0, KICK_VV = 1, KICK_NH = 2, KICK_NH_EXACT = 3 };
@@ -94,96 +98,112 @@ __device__ int grid_sync(const KParams& p, Shared& sh, int where) {
   return sh.snap;
 }
 
+// Float-float (compensated) addition: exact TwoSum of the high parts, low
+// parts added with the rounding error, then renormalised. Commutative, so
+// an xor-butterfly leaves the same value in every lane.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = (a.lo + b.lo) + e;
+  const float h = s + lo;
+  return {h, lo - (h - s)};
+}
+__device__ __forceinline__ ff warp_sum_ff(ff v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = ff_add(v, w);
+  }
+  return v;
+}
+
 __device__ __forceinline__ void raise_flag(const KParams& p, int f) {
   if (!(vload_i32(&p.ctl->pending) & f)) atomicOr(&p.ctl->pending, f);
 }
 
 // ------------------------------------------------------------------ drift
 
-// Position update of one particle. Mixed: FP32 increment added to the 64-bit
-// fixed-point coordinate (wrap = integer overflow, image counted from the
-// carry). FP64: double increment, wrap into [0, L).
-template <bool MIX>
-__device__ __forceinline__ void drift_atom(const KParams& p, const RepDev& R, int64_t i, int cur,
-                                           double vx, double vy, double vz, double ax, double ay, double az,
-                                           double xi, uint32_t type) {
+// Position update of one particle, mixed path: an FP32 increment is turned
+// into a 64-bit fixed-point step with 32-bit conversions only (x = d 2^32/L,
+// high word floor(x), low word from the fraction) and added to the integer
+// coordinate; the wrap is the integer overflow and the image counter follows
+// the carry. Also refreshes the gather copy and checks the half-skin trigger.
+__device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int64_t i, int cur, const float v[3],
+                                          const float a[3], float xi, uint32_t type) {
   const int64_t nt = p.ntot;
-  if constexpr (MIX) {
-    const float dt = (float)p.dt, hdt2 = 0.5f * (float)p.dt * (float)p.dt, xif = (float)xi;
-    const float fv[3] = {(float)vx, (float)vy, (float)vz};
-    const float fa[3] = {(float)ax, (float)ay, (float)az};
-    float d[3];
-    bool bad = false;
+  const float dt = p.dtf, hdt2 = 0.5f * p.dtf * p.dtf;
+  float d[3];
+  bool bad = false;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      d[c] = fmaf(fv[c], dt, (fa[c] - xif * fv[c]) * hdt2);
-      bad |= !(fabsf(d[c]) < 0.25f * R.Lf);
-    }
-    if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
-    uint32_t hi[3];
+  for (int c = 0; c < 3; ++c) {
+    d[c] = fmaf(v[c], dt, (a[c] - xi * v[c]) * hdt2);
+    bad |= !(fabsf(d[c]) < 0.25f * R.Lf);
+  }
+  if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
+  uint32_t hi[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const uint64_t u = p.pfx[c * nt + i];
-      const long long du = __float2ll_rn(d[c] * R.fx64f);
-      const uint64_t un = u + (uint64_t)du;
-      if (du > 0 && un < u) p.img[c * nt + i] += 1;
-      else if (du < 0 && un > u) p.img[c * nt + i] -= 1;
-      p.pfx[c * nt + i] = un;
-      hi[c] = (uint32_t)(un >> 32);
-    }
-    p.pq[cur ^ 1][i] = make_uint4(hi[0], hi[1], hi[2], type);
-    const uint4 xb = p.xbq[i];
-    const float ex = (float)(int)(hi[0] - xb.x) * R.fxs;
-    const float ey = (float)(int)(hi[1] - xb.y) * R.fxs;
-    const float ez = (float)(int)(hi[2] - xb.z) * R.fxs;
-    if (ex * ex + ey * ey + ez * ez > (float)p.skin_half2) {
-      p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
-      raise_flag(p, MD_FLAG_REBUILD);
-    }
-  } else {
-    const double dt = p.dt, hdt2 = 0.5 * p.dt * p.dt;
-    double4_32a x = p.p4[cur][i];
-    double d[3] = {vx * dt + (ax - xi * vx) * hdt2, vy * dt + (ay - xi * vy) * hdt2, vz * dt + (az - xi * vz) * hdt2};
-    bool bad = false;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) bad |= !(fabs(d[c]) < 0.25 * R.L);
-    if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
-    double xs[3] = {x.x + d[0], x.y + d[1], x.z + d[2]};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
-      else if (xs[c] < 0.0) {
-        xs[c] += R.L; p.img[c * nt + i] -= 1;
-        if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
-      }
-    }
-    p.p4[cur ^ 1][i] = make_double4_32a(xs[0], xs[1], xs[2], x.w);
-    const double4_32a xb = p.xbd[i];
-    double e[3] = {xs[0] - xb.x, xs[1] - xb.y, xs[2] - xb.z};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (e[c] > 0.5 * R.L) e[c] -= R.L;
-      else if (e[c] < -0.5 * R.L) e[c] += R.L;
-    }
-    if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] > p.skin_half2) {
-      p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
-      raise_flag(p, MD_FLAG_REBUILD);
-    }
+  for (int c = 0; c < 3; ++c) {
+    const float x = d[c] * R.fx32f;
+    const float xh = floorf(x);
+    const float fr = x - xh;  // exact, in [0, 1)
+    const uint32_t lo = __float2uint_rn(fr * 4294967296.0f);
+    const long long du = (long long)((uint64_t)(uint32_t)__float2int_rn(xh) << 32) + (long long)lo;
+    const uint64_t u = p.pfx[c * nt + i];
+    const uint64_t un = u + (uint64_t)du;
+    if (du > 0 && un < u) p.img[c * nt + i] += 1;
+    else if (du < 0 && un > u) p.img[c * nt + i] -= 1;
+    p.pfx[c * nt + i] = un;
+    hi[c] = (uint32_t)(un >> 32);
+  }
+  p.pq[cur ^ 1][i] = make_uint4(hi[0], hi[1], hi[2], type);
+  const uint4 xb = p.xbq[i];
+  const float ex = (float)(int)(hi[0] - xb.x) * R.fxs;
+  const float ey = (float)(int)(hi[1] - xb.y) * R.fxs;
+  const float ez = (float)(int)(hi[2] - xb.z) * R.fxs;
+  if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > p.skin_half2f) {
+    p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
+    raise_flag(p, MD_FLAG_REBUILD);
   }
 }
 
-template <bool MIX>
-__device__ __forceinline__ void load_va(const KParams& p, int64_t i, double v[3], double a[3]) {
+// Position update of one particle, FP64 path: wrap into [0, L).
+__device__ __forceinline__ void drift_f64(const KParams& p, const RepDev& R, int64_t i, int cur, const double v[3],
+                                          const double a[3], double xi) {
   const int64_t nt = p.ntot;
+  const double dt = p.dt, hdt2 = 0.5 * p.dt * p.dt;
+  const double4_32a x = p.p4[cur][i];
+  double d[3];
+  bool bad = false;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if constexpr (MIX) {
-      v[c] = p.velf[c * nt + i];
-      a[c] = (double)(p.frcf[c * nt + i] * (float)p.inv_mass);
-    } else {
-      v[c] = p.veld[c * nt + i];
-      a[c] = p.frcd[c * nt + i] * p.inv_mass;
+    d[c] = v[c] * dt + (a[c] - xi * v[c]) * hdt2;
+    bad |= !(fabs(d[c]) < 0.25 * R.L);
+  }
+  if (bad) { raise_flag(p, MD_FLAG_UNSTABLE); return; }
+  double xs[3] = {x.x + d[0], x.y + d[1], x.z + d[2]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
+    else if (xs[c] < 0.0) {
+      xs[c] += R.L; p.img[c * nt + i] -= 1;
+      if (xs[c] >= R.L) { xs[c] -= R.L; p.img[c * nt + i] += 1; }
     }
+  }
+  p.p4[cur ^ 1][i] = make_double4_32a(xs[0], xs[1], xs[2], x.w);
+  const double4_32a xb = p.xbd[i];
+  double e[3] = {xs[0] - xb.x, xs[1] - xb.y, xs[2] - xb.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (e[c] > 0.5 * R.L) e[c] -= R.L;
+    else if (e[c] < -0.5 * R.L) e[c] += R.L;
+  }
+  if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] > p.skin_half2) {
+    p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
+    raise_flag(p, MD_FLAG_REBUILD);
   }
 }
 
@@ -193,39 +213,74 @@ __device__ __forceinline__ void load_va(const KParams& p, int64_t i, double v[3]
 template <bool MIX>
 __device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bool drift) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ntot; i += stride) {
+  const int64_t nt = p.ntot;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += stride) {
     const RepDev& R = p.reps[p.tile_rep[i >> 5]];
     if (i - R.off >= R.n) continue;
-    double v[3], a[3];
-    load_va<MIX>(p, i, v, a);
-    if (rescale) {
-      const int64_t nt = p.ntot;
+    if constexpr (MIX) {
+      float v[3], a[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if constexpr (MIX) {
-          const float vf = ((float)v[c] - (float)R.vmean[c]) * (float)R.vscale;
-          p.velf[c * nt + i] = vf;
-          v[c] = vf;
-        } else {
+        v[c] = p.velf[c * nt + i];
+        a[c] = p.frcf[c * nt + i] * p.inv_massf;
+      }
+      if (rescale) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          v[c] = (v[c] - R.vmeanf[c]) * R.vscalef;
+          p.velf[c * nt + i] = v[c];
+        }
+      }
+      if (drift) drift_mix(p, R, i, cur, v, a, nh ? R.xif : 0.0f, p.pq[cur][i].w);
+    } else {
+      double v[3], a[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[c] = p.veld[c * nt + i];
+        a[c] = p.frcd[c * nt + i] * p.inv_mass;
+      }
+      if (rescale) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
           v[c] = (v[c] - R.vmean[c]) * R.vscale;
           p.veld[c * nt + i] = v[c];
         }
       }
-    }
-    if (drift) {
-      uint32_t type;
-      if constexpr (MIX) type = p.pq[cur][i].w; else type = 0;
-      drift_atom<MIX>(p, R, i, cur, v[0], v[1], v[2], a[0], a[1], a[2], nh ? R.xi : 0.0, type);
+      if (drift) drift_f64(p, R, i, cur, v, a, nh ? R.xi : 0.0);
     }
   }
 }
 
 // ------------------------------------------------------------------ forces
 
-// Sum the per-lane energies of one tile (T warps) in a fixed order and store
-// the tile's partials. Every thread of the block calls this.
-__device__ __forceinline__ void tile_partials(const KParams& p, Shared& sh, double* part, int tile, bool valid,
-                                              int T, double e[6]) {
+// Per-tile partial sums (PE, KE, virial, momentum). Every thread of the
+// block calls these. Mixed: float-float warp sums, stored as (hi, lo) pairs.
+// FP64: double warp sums. The T warps of a tile are combined in order.
+__device__ __forceinline__ void tile_partials_ff(Shared& sh, double* part, int tile, bool valid, int T,
+                                                 const float e[6]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* red = reinterpret_cast<float2*>(&sh.red[0][0]);
+  ff w[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) w[k] = warp_sum_ff(ff{e[k], 0.0f});
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) red[warp * MD_NPART + k] = make_float2(w[k].hi, w[k].lo);
+  }
+  __syncthreads();
+  if (valid && (threadIdx.x % (32 * T)) == 0) {
+    float2* out = reinterpret_cast<float2*>(part) + (int64_t)tile * MD_NPART;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      ff acc = {red[warp * MD_NPART + k].x, red[warp * MD_NPART + k].y};
+      for (int q = 1; q < T; ++q) acc = ff_add(acc, ff{red[(warp + q) * MD_NPART + k].x, red[(warp + q) * MD_NPART + k].y});
+      out[k] = make_float2(acc.hi, acc.lo);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void tile_partials_d(Shared& sh, double* part, int tile, bool valid, int T, double e[6]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 6; ++k) e[k] = warp_sum(e[k]);
@@ -234,19 +289,22 @@ __device__ __forceinline__ void tile_partials(const KParams& p, Shared& sh, doub
     for (int k = 0; k < 6; ++k) sh.red[warp][k] = e[k];
   }
   __syncthreads();
-  const int gsz = 32 * T;
-  if (valid && (threadIdx.x % gsz) == 0) {
-    const int w0 = warp;
+  if (valid && (threadIdx.x % (32 * T)) == 0) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < T; ++w)
+    for (int q = 0; q < T; ++q)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] += sh.red[w0 + w][k];
+      for (int k = 0; k < 6; ++k) acc[k] += sh.red[warp + q][k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) part[(int64_t)tile * MD_NPART + k] = acc[k];
   }
   __syncthreads();
 }
 
+// Force phase. Lane s of particle a walks its own column of the list; the T
+// lanes are combined by a fixed xor tree; lane 0 then applies the velocity
+// rule of `kick`, stores force and velocity, and (if `fuse`) already performs
+// the next position update into the other gather buffer. Without `pairs`
+// only the kinetic partials are formed (forces known, velocities unchanged).
 template <bool MIX>
 __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs) {
   const int T = p.T;
@@ -259,7 +317,6 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
   for (int base = blockIdx.x * tpb; base < p.ntiles; base += gridDim.x * tpb) {
     const int tile = base + tib;
     const bool valid = tile < p.ntiles;
-    double e[6] = {0, 0, 0, 0, 0, 0};
     const RepDev* R = nullptr;
     bool act = false;
     int64_t i = 0;
@@ -268,22 +325,20 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
       act = (tile - R->tile0) * 32 + a < R->n;
       i = (int64_t)tile * 32 + a;
     }
-    // ---- pair loop (each of the T lanes takes every T-th list entry)
-    double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
-    uint32_t type_i = 0;
-    if (act && pairs) {
-      const int cnt = p.nnb[i];
-      const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
-      if constexpr (MIX) {
+    const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
+    const int cnt = (act && pairs) ? p.nnb[i * T + s] : 0;
+    if constexpr (MIX) {
+      float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, vir = 0.f;
+      uint32_t type_i = 0;
+      if (act) {
         const uint4* __restrict__ pq = p.pq[cur];
         const uint4 pi = pq[i];
         type_i = pi.w;
         const int tb = (int)pi.w * p.ntypes;
         const float sc = R->fxs;
-        float ffx = 0.f, ffy = 0.f, ffz = 0.f, fpe = 0.f, fvir = 0.f;
 #pragma unroll 4
-        for (int k = s; k < cnt; k += T, lp += gsz) {
-          const int j = *lp;
+        for (int q = 0; q < cnt; ++q) {
+          const int j = lp[q * gsz];
           const uint4 pj = pq[j];
           const float dx = (float)(int)(pi.x - pj.x) * sc;
           const float dy = (float)(int)(pi.y - pj.y) * sc;
@@ -297,21 +352,57 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
           const float w = c.z * s6 * (s6 - 0.5f);
           const bool in = r2 < c.x;
           const float fr = in ? w * ir2 : 0.0f;
-          ffx = fmaf(fr, dx, ffx);
-          ffy = fmaf(fr, dy, ffy);
-          ffz = fmaf(fr, dz, ffz);
-          fpe += in ? fmaf(c.w * s6, s6 - 1.0f, -sh.vshf[tt]) : 0.0f;
-          fvir += in ? w : 0.0f;
+          fx = fmaf(fr, dx, fx);
+          fy = fmaf(fr, dy, fy);
+          fz = fmaf(fr, dz, fz);
+          pe += in ? fmaf(c.w * s6, s6 - 1.0f, -sh.vshf[tt]) : 0.0f;
+          vir += in ? w : 0.0f;
         }
-        fx = ffx; fy = ffy; fz = ffz; pe = fpe; vir = fvir;
-      } else {
+      }
+      for (int o = T >> 1; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        pe += __shfl_xor_sync(0xffffffffu, pe, o);
+        vir += __shfl_xor_sync(0xffffffffu, vir, o);
+      }
+      float e[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (act && s == 0) {
+        const float im = p.inv_massf, hdt = 0.5f * p.dtf, m = p.massf;
+        const float xi = R->xif, xia = R->xiaf;
+        const float F[3] = {fx, fy, fz};
+        float v[3], an[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float vf = p.velf[c * nt + i];
+          const float ao = p.frcf[c * nt + i] * im;
+          const float af = F[c] * im;
+          an[c] = af;
+          if (kick == KICK_VV) vf = fmaf(hdt, ao + af, vf);
+          else if (kick == KICK_NH) vf = vf + hdt * ((ao + af) - (xi + xia) * vf) * (1.0f - hdt * xia);
+          else if (kick == KICK_NH_EXACT) vf = (vf + hdt * (ao - xi * vf + af)) / (1.0f + hdt * xia);
+          v[c] = vf;
+          if (pairs) p.frcf[c * nt + i] = F[c];
+          if (kick != KICK_NONE) p.velf[c * nt + i] = vf;
+        }
+        e[0] = 0.5f * pe;
+        e[1] = 0.5f * m * fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2]));
+        e[2] = 0.5f * vir;
+        e[3] = m * v[0];
+        e[4] = m * v[1];
+        e[5] = m * v[2];
+        if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, type_i);
+      }
+      tile_partials_ff(sh, part, tile, valid, T, e);
+    } else {
+      double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
+      if (act) {
         const double4_32a* __restrict__ p4 = p.p4[cur];
         const double4_32a pi = p4[i];
-        type_i = (uint32_t)pi.w;
         const int tb = (int)pi.w * p.ntypes;
         const double L = R->L, hL = 0.5 * R->L;
-        for (int k = s; k < cnt; k += T, lp += gsz) {
-          const int j = *lp;
+        for (int q = 0; q < cnt; ++q) {
+          const int j = lp[q * gsz];
           const double4_32a pj = p4[j];
           double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
@@ -332,63 +423,42 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
           }
         }
       }
-    }
-    // ---- combine the T lanes of each particle (fixed xor order)
-    for (int o = T >> 1; o > 0; o >>= 1) {
-      fx += __shfl_xor_sync(0xffffffffu, fx, o);
-      fy += __shfl_xor_sync(0xffffffffu, fy, o);
-      fz += __shfl_xor_sync(0xffffffffu, fz, o);
-      pe += __shfl_xor_sync(0xffffffffu, pe, o);
-      vir += __shfl_xor_sync(0xffffffffu, vir, o);
-    }
-    // ---- velocity update, stores, energies, fused drift (one lane per particle)
-    if (act && s == 0) {
-      double v[3], ao[3];
-      load_va<MIX>(p, i, v, ao);
-      const double F[3] = {fx, fy, fz};
-      double an[3];
-      if constexpr (MIX) {
-        const float im = (float)p.inv_mass, hdt = 0.5f * (float)p.dt;
-        const float xi = (float)R->xi, xia = (float)R->xi_a;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float af = (float)F[c] * im;
-          an[c] = af;
-          float vf = (float)v[c];
-          const float aof = (float)ao[c];
-          if (kick == KICK_VV) vf = fmaf(hdt, aof + af, vf);
-          else if (kick == KICK_NH) vf = vf + hdt * ((aof + af) - (xi + xia) * vf) * (1.0f - hdt * xia);
-          else if (kick == KICK_NH_EXACT) vf = (vf + hdt * (aof - xi * vf + af)) / (1.0f + hdt * xia);
-          v[c] = vf;
-          if (pairs) p.frcf[c * nt + i] = (float)F[c];
-          if (kick != KICK_NONE) p.velf[c * nt + i] = vf;
-        }
-      } else {
-        const double im = p.inv_mass, hdt = 0.5 * p.dt;
+      for (int o = T >> 1; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        pe += __shfl_xor_sync(0xffffffffu, pe, o);
+        vir += __shfl_xor_sync(0xffffffffu, vir, o);
+      }
+      double e[6] = {0, 0, 0, 0, 0, 0};
+      if (act && s == 0) {
+        const double im = p.inv_mass, hdt = 0.5 * p.dt, m = p.mass;
         const double xi = R->xi, xia = R->xi_a;
+        const double F[3] = {fx, fy, fz};
+        double v[3], an[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          double vd = p.veld[c * nt + i];
+          const double ao = p.frcd[c * nt + i] * im;
           const double ad = F[c] * im;
           an[c] = ad;
-          double vd = v[c];
-          if (kick == KICK_VV) vd = vd + hdt * (ao[c] + ad);
-          else if (kick == KICK_NH) vd = vd + hdt * ((ao[c] + ad) - (xi + xia) * vd) * (1.0 - hdt * xia);
-          else if (kick == KICK_NH_EXACT) vd = (vd + hdt * (ao[c] - xi * vd + ad)) / (1.0 + hdt * xia);
+          if (kick == KICK_VV) vd = vd + hdt * (ao + ad);
+          else if (kick == KICK_NH) vd = vd + hdt * ((ao + ad) - (xi + xia) * vd) * (1.0 - hdt * xia);
+          else if (kick == KICK_NH_EXACT) vd = (vd + hdt * (ao - xi * vd + ad)) / (1.0 + hdt * xia);
           v[c] = vd;
           if (pairs) p.frcd[c * nt + i] = F[c];
           if (kick != KICK_NONE) p.veld[c * nt + i] = vd;
         }
+        e[0] = 0.5 * pe;
+        e[1] = 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        e[2] = 0.5 * vir;
+        e[3] = m * v[0];
+        e[4] = m * v[1];
+        e[5] = m * v[2];
+        if (fuse) drift_f64(p, *R, i, cur, v, an, 0.0);
       }
-      const double m = p.mass;
-      e[0] = 0.5 * pe;
-      e[1] = 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      e[2] = 0.5 * vir;
-      e[3] = m * v[0];
-      e[4] = m * v[1];
-      e[5] = m * v[2];
-      if (fuse) drift_atom<MIX>(p, *R, i, cur, v[0], v[1], v[2], an[0], an[1], an[2], 0.0, type_i);
+      tile_partials_d(sh, part, tile, valid, T, e);
     }
-    tile_partials(p, sh, part, tile, valid, T, e);
   }
 }
 
@@ -396,6 +466,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
 
 // Draw Maxwell-Boltzmann velocities (step 1 of the flow chart in Sec.
 // "Statistical temperature bath") and store per-tile sums of v and v^2.
+// One warp per tile.
 template <bool MIX>
 __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* part) {
   const int lane = threadIdx.x & 31;
@@ -404,30 +475,44 @@ __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* par
   for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < p.ntiles; tile += nw) {
     const RepDev& R = p.reps[p.tile_rep[tile]];
     const int64_t i = tile * 32 + lane;
-    double e[4] = {0, 0, 0, 0};
-    if (i - R.off < R.n) {
-      double g[3];
-      gauss3(p.seed, draw, (uint32_t)(p.gid[i] - R.out0), g);
-      const double sd = sqrt(R.T_target * p.inv_mass);
+    const bool act = i - R.off < R.n;
+    double g[3] = {0, 0, 0};
+    if (act) gauss3(p.seed, draw, (uint32_t)(p.gid[i] - R.out0), g);
+    if constexpr (MIX) {
+      float e[4] = {0.f, 0.f, 0.f, 0.f};
+      if (act) {
+        const float sd = sqrtf((float)R.T_target * p.inv_massf);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double v = sd * g[c];
-        if constexpr (MIX) {
-          const float vf = (float)v;
-          p.velf[c * nt + i] = vf;
-          v = vf;
-        } else {
-          p.veld[c * nt + i] = v;
+        for (int c = 0; c < 3; ++c) {
+          const float v = sd * (float)g[c];
+          p.velf[c * nt + i] = v;
+          e[c] = v;
+          e[3] = fmaf(v, v, e[3]);
         }
-        e[c] = v;
-        e[3] += v * v;
       }
-    }
+      float2* out = reinterpret_cast<float2*>(part) + tile * MD_NPART;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e[k] = warp_sum(e[k]);
-    if (lane == 0) {
+      for (int k = 0; k < 4; ++k) {
+        const ff w = warp_sum_ff(ff{e[k], 0.0f});
+        if (lane == 0) out[k] = make_float2(w.hi, w.lo);
+      }
+    } else {
+      double e[4] = {0, 0, 0, 0};
+      if (act) {
+        const double sd = sqrt(R.T_target * p.inv_mass);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) part[tile * MD_NPART + k] = e[k];
+        for (int c = 0; c < 3; ++c) {
+          const double v = sd * g[c];
+          p.veld[c * nt + i] = v;
+          e[c] = v;
+          e[3] += v * v;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double w = warp_sum(e[k]);
+        if (lane == 0) part[tile * MD_NPART + k] = w;
+      }
     }
   }
 }
@@ -437,8 +522,10 @@ __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* par
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh);
 
-// One warp per replica: fixed-order sum of the replica's tile partials, then
-// the scalar updates of the mode and, if asked, one thermo record.
+// One warp per replica: fixed-order sum of the replica's tile partials
+// (float-float for the mixed path, double for FP64), then the scalar updates
+// of the mode and, if asked, one thermo record.
+template <bool MIX>
 __device__ void reduce_phase(const KParams& p, const double* part, int mode, int64_t step, bool log_now,
                              int64_t log_idx) {
   const int lane = threadIdx.x & 31;
@@ -446,57 +533,78 @@ __device__ void reduce_phase(const KParams& p, const double* part, int mode, int
   const bool nh = (p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT) && p.op == MD_OP_STEPS;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < p.nrep; r += nw) {
     RepDev& R = p.reps[r];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int t = lane; t < R.ntiles; t += 32) {
-      const double* q = part + (int64_t)(R.tile0 + t) * MD_NPART;
+    double acc[6];
+    if constexpr (MIX) {
+      ff a[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] += q[k];
+      for (int k = 0; k < 6; ++k) a[k] = ff{0.f, 0.f};
+      const float2* q0 = reinterpret_cast<const float2*>(part);
+      for (int t = lane; t < R.ntiles; t += 32) {
+        const float2* q = q0 + (int64_t)(R.tile0 + t) * MD_NPART;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = ff_add(a[k], ff{q[k].x, q[k].y});
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        a[k] = warp_sum_ff(a[k]);
+        acc[k] = (double)a[k].hi + (double)a[k].lo;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+      for (int t = lane; t < R.ntiles; t += 32) {
+        const double* q = part + (int64_t)(R.tile0 + t) * MD_NPART;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += q[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
     if (lane == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
   }
 }
 
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh) {
-  {
-    const double n = (double)R.n, X = 3.0 * n, dt = p.dt;
-    if (mode == RED_RESAMPLE) {
-      const double mx = acc[0] / n, my = acc[1] / n, mz = acc[2] / n;
-      const double S = acc[3] - n * (mx * mx + my * my + mz * mz);
-      const double sc = (S > 0.0) ? sqrt(X * R.T_target / (p.mass * S)) : 0.0;
-      R.vmean[0] = mx; R.vmean[1] = my; R.vmean[2] = mz;
-      R.vscale = sc;
-      R.ke = 0.5 * p.mass * sc * sc * S;
-      R.px = R.py = R.pz = 0.0;
-    } else {
-      if (mode == RED_FORCES || mode == RED_STEP) { R.pe = acc[0]; R.vir = acc[2]; }
-      R.ke = acc[1];
-      R.px = acc[3]; R.py = acc[4]; R.pz = acc[5];
-      if (nh) {
-        const double gnew = (2.0 * R.ke - X * R.T_target) / R.Q;
-        if (mode == RED_STEP) {
-          R.xi = R.xi + 0.5 * dt * (R.g + gnew);  // Eq. (FoxAndersen_ydottplush)
-          R.lns = R.lns_next;
-        }
-        R.g = gnew;
-        R.xi_a = R.xi + dt * R.g;                              // Eq. (Noseupdate_xiapprox)
-        R.lns_next = R.lns + R.xi * dt + 0.5 * R.g * dt * dt;  // Eq. (Noseupdate_lns)
+  const double n = (double)R.n, X = 3.0 * n, dt = p.dt;
+  if (mode == RED_RESAMPLE) {
+    const double mx = acc[0] / n, my = acc[1] / n, mz = acc[2] / n;
+    const double S = acc[3] - n * (mx * mx + my * my + mz * mz);
+    const double sc = (S > 0.0) ? sqrt(X * R.T_target / (p.mass * S)) : 0.0;
+    R.vmean[0] = mx; R.vmean[1] = my; R.vmean[2] = mz;
+    R.vscale = sc;
+    R.vmeanf[0] = (float)mx; R.vmeanf[1] = (float)my; R.vmeanf[2] = (float)mz;
+    R.vscalef = (float)sc;
+    R.ke = 0.5 * p.mass * sc * sc * S;
+    R.px = R.py = R.pz = 0.0;
+  } else {
+    if (mode == RED_FORCES || mode == RED_STEP) { R.pe = acc[0]; R.vir = acc[2]; }
+    R.ke = acc[1];
+    R.px = acc[3]; R.py = acc[4]; R.pz = acc[5];
+    if (nh) {
+      const double gnew = (2.0 * R.ke - X * R.T_target) / R.Q;
+      if (mode == RED_STEP) {
+        R.xi = R.xi + 0.5 * dt * (R.g + gnew);  // Eq. (FoxAndersen_ydottplush)
+        R.lns = R.lns_next;
       }
+      R.g = gnew;
+      R.xi_a = R.xi + dt * R.g;                              // Eq. (Noseupdate_xiapprox)
+      R.lns_next = R.lns + R.xi * dt + 0.5 * R.g * dt * dt;  // Eq. (Noseupdate_lns)
+      R.xif = (float)R.xi;
+      R.xiaf = (float)R.xi_a;
     }
-    if (log_now && p.thermo) {
-      ThermoDev th;
-      th.step = step;
-      th.T = 2.0 * R.ke / X;
-      th.pe_per_n = R.pe / n;
-      th.ke_per_n = R.ke / n;
-      th.etot_per_n = (R.ke + R.pe) / n;
-      th.virial = R.vir;
-      th.h_nh = R.ke + R.pe + (nh ? 0.5 * R.Q * R.xi * R.xi + X * R.T_target * R.lns : 0.0);
-      th.xi = nh ? R.xi : 0.0;
-      p.thermo[log_idx * p.nrep + r] = th;
-    }
+  }
+  if (log_now && p.thermo) {
+    ThermoDev th;
+    th.step = step;
+    th.T = 2.0 * R.ke / X;
+    th.pe_per_n = R.pe / n;
+    th.ke_per_n = R.ke / n;
+    th.etot_per_n = (R.ke + R.pe) / n;
+    th.virial = R.vir;
+    th.h_nh = R.ke + R.pe + (nh ? 0.5 * R.Q * R.xi * R.xi + X * R.T_target * R.lns : 0.0);
+    th.xi = nh ? R.xi : 0.0;
+    p.thermo[log_idx * p.nrep + r] = th;
   }
 }
 
@@ -575,7 +683,6 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
     if (threadIdx.x == 0) {
       R.want_rebuild = 0;
       R.rebuilds += 1;
-      R.list_entries = 0;
     }
     if (R.nc == 0) continue;
     const int ncell = R.nc * R.nc * R.nc;
@@ -667,15 +774,18 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
   f = grid_sync(p, sh, 105);
   if (f < 0) return false;
   // B6: Verlet list over the 27 neighbouring cells (or all particles of a
-  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin.
+  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. The T
+  // lanes of a particle split the candidate sequence round-robin; lane s
+  // keeps every candidate whose running index is s mod T, in its own column.
   const int T = p.T, gsz = 32 * T;
-  const int cap = p.maxrows * T;
-  for (int64_t i = gtid; i < nt; i += stride) {
-    RepDev& R = p.reps[p.tile_rep[i >> 5]];
+  const int cap = p.maxrows;
+  for (int64_t idx = gtid; idx < nt * T; idx += stride) {
+    const int64_t i = idx / T;
+    const int s = (int)(idx - i * T);
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
     if (i - R.off >= R.n || !R.doing_rebuild) continue;
-    const int a = (int)(i & 31);
-    int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + a * T;
-    int k = 0;
+    int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + s;
+    int k = 0, base = 0;
     int cx = 0, cy = 0, cz = 0;
     const int nc = R.nc;
     if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
@@ -695,19 +805,20 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
           lo = (int)R.off;
           hi = (int)(R.off + R.n);
         }
-        for (int j = lo; j < hi; ++j) {
+        for (int j = lo + ((s - base % T) + T) % T; j < hi; j += T) {
           if (j == i) continue;
           const uint4 pj = p.pq[cur][j];
           const float dx = (float)(int)(pi.x - pj.x) * sc;
           const float dy = (float)(int)(pi.y - pj.y) * sc;
           const float dz = (float)(int)(pi.z - pj.z) * sc;
           if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
-            if (k < cap) lb[(k / T) * gsz + (k % T)] = j;
+            if (k < cap) lb[(int64_t)k * gsz] = j;
             ++k;
           }
         }
+        base += hi - lo;
       }
-      p.xbq[i] = pi;
+      if (s == 0) p.xbq[i] = pi;
     } else {
       const double4_32a pi = p.p4[cur][i];
       const int tb = (int)pi.w * p.ntypes;
@@ -723,7 +834,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
           lo = (int)R.off;
           hi = (int)(R.off + R.n);
         }
-        for (int j = lo; j < hi; ++j) {
+        for (int j = lo + ((s - base % T) + T) % T; j < hi; j += T) {
           if (j == i) continue;
           const double4_32a pj = p.p4[cur][j];
           double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -731,16 +842,16 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
           if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
           if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
           if (dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
-            if (k < cap) lb[(k / T) * gsz + (k % T)] = j;
+            if (k < cap) lb[(int64_t)k * gsz] = j;
             ++k;
           }
         }
+        base += hi - lo;
       }
-      p.xbd[i] = pi;
+      if (s == 0) p.xbd[i] = pi;
     }
     if (k > cap) raise_flag(p, MD_FLAG_OVERFLOW);
-    p.nnb[i] = min(k, cap);
-    atomicAdd((unsigned long long*)&R.list_entries, (unsigned long long)min(k, cap));
+    p.nnb[i * T + s] = min(k, cap);
   }
   f = grid_sync(p, sh, 106);
   if (f < 0) return false;
@@ -751,7 +862,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
 // ------------------------------------------------------------------ kernel
 
 template <bool MIX>
-__global__ void __launch_bounds__(512) md_persistent(KParams p) {
+__global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p) {
   __shared__ Shared sh;
   const int nt2 = p.ntypes * p.ntypes;
   for (int t = threadIdx.x; t < nt2; t += blockDim.x) {
@@ -798,7 +909,7 @@ __global__ void __launch_bounds__(512) md_persistent(KParams p) {
       // then centre and rescale (steps 1-4 of Sec. "Statistical temperature bath")
       resample_draw_phase<MIX>(p, 0, p.part[0]);
       if ((fl = grid_sync(p, sh, 2)) < 0) return;
-      reduce_phase(p, p.part[0], RED_RESAMPLE, step0, false, 0);
+      reduce_phase<MIX>(p, p.part[0], RED_RESAMPLE, step0, false, 0);
       if ((fl = grid_sync(p, sh, 3)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, false);
       finish(false, fvalid);
@@ -807,7 +918,7 @@ __global__ void __launch_bounds__(512) md_persistent(KParams p) {
     const bool pairs = !fvalid || p.op == MD_OP_FORCES;
     force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs);
     if ((fl = grid_sync(p, sh, 4)) < 0) return;
-    reduce_phase(p, p.part[0], pairs ? RED_FORCES : RED_KE, step0, false, 0);
+    reduce_phase<MIX>(p, p.part[0], pairs ? RED_FORCES : RED_KE, step0, false, 0);
     if ((fl = grid_sync(p, sh, 5)) < 0) return;
     if (p.op == MD_OP_FORCES || p.nsteps == 0) { finish(false, 1); return; }
     drift_phase<MIX>(p, cur, nh, false, true);
@@ -833,7 +944,7 @@ __global__ void __launch_bounds__(512) md_persistent(KParams p) {
     const int64_t li = p.log_step0 + s + 1;
     const bool log_now = p.log_every > 0 && (li % p.log_every) == 0 && (li / p.log_every - 1) < p.log_cap;
     const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
-    if (log_now || nh || last || rs) reduce_phase(p, part, RED_STEP, step, log_now && !rs, lidx);
+    if (log_now || nh || last || rs) reduce_phase<MIX>(p, part, RED_STEP, step, log_now && !rs, lidx);
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
@@ -847,7 +958,7 @@ __global__ void __launch_bounds__(512) md_persistent(KParams p) {
       double* part2 = p.part[(step & 1) ^ 1];
       resample_draw_phase<MIX>(p, (uint64_t)(step / p.nstep_boltz), part2);
       if ((fl = grid_sync(p, sh, 14)) < 0) return;
-      reduce_phase(p, part2, RED_RESAMPLE, step, log_now, lidx);
+      reduce_phase<MIX>(p, part2, RED_RESAMPLE, step, log_now, lidx);
       if ((fl = grid_sync(p, sh, 15)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, !last);
       if (!last) { cur ^= 1; now_drifted = true; }

@@ -68,11 +68,32 @@ def test_forces_every_lane_split(prec, tpa):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_forces_32k_jittered_lattice(prec):
+def test_forces_32k_tiled_melt(prec):
+    """N = 32 000 at rho = 1.2: an oracle-melted N = 4000 liquid tiled 2x2x2 (every particle keeps
+    its environment because r_c < L_4000/2, so the oracle also checks replication invariance)."""
+    pos4, vel4, types4, L4 = melted(4000, 23, nsteps=200)
+    shifts = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], dtype=float) * L4
+    pos = np.concatenate([pos4 + sh for sh in shifts])
+    vel = np.concatenate([vel4] * 8)
+    types = np.concatenate([types4] * 8)
+    L = 2 * L4
+    f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
+    f4, v4, _ = oracle.forces(pos4, types4, ka_params(), L4)
+    assert np.max(np.abs(f_ref - np.concatenate([f4] * 8))) < 1e-9 * np.abs(f4).max()
+    with make_system(32000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        f, pe, _ = s.forces()
+    check_forces(f, f_ref, prec)
+    assert abs(pe[0] - v_ref) <= TOL_E[prec] * abs(v_ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_32k_lattice_start(prec):
+    """The 32k configuration's own start: 32^3 lattice sites (32 000 occupied), jitter 0.05."""
     n = 32000
     L = wl.box_length(n)
     types = wl.ka_types(n, 25).astype(np.int32)
-    pos, vel = oracle.init_lattice(n, L, 2.0, seed=25, jitter=0.2)
+    pos, vel = oracle.init_lattice(n, L, 2.0, seed=25, jitter=0.05)
     f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
     with make_system(n, L, types, prec) as s:
         s.set_state(pos, vel)
@@ -225,15 +246,25 @@ def test_batch_replicas_equal_standalone_runs(prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_rebuilds_keep_parity_over_long_nve(prec):
-    """400 NVE steps at T=2 cross many list rebuilds; the energy trace stays on the oracle's."""
+    """400 NVE steps at T=2 cross many list rebuilds. FP64 follows the oracle step by step; the
+    mixed path does for the first 100 steps, after which chaos amplifies FP32 rounding and the
+    comparison is the size of the energy excursions (the conservation statistics)."""
     pos, vel, types, L = melted(1000, 71, nsteps=100)
-    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 400, log_every=20)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 400, log_every=1)
     with make_system(1000, L, types, prec) as s:
         s.set_state(pos, vel)
-        log = s.step_nve(0.005, 400, log_every=20)
+        log = s.step_nve(0.005, 400, log_every=1)
         info = s.info()
     assert info["rebuilds"] >= 5
-    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= (1e-9 if prec == "fp64" else 1e-5)
+    if prec == "fp64":
+        assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= 1e-9
+    else:
+        assert thermo_rel(log[:100], ref["thermo"][:100], "etot_per_n", 4) <= TOL_E["mixed"]
+        e_g = log["etot_per_n"][:, 0]
+        e_r = ref["thermo"][:, 4]
+        exc_g = np.max(np.abs(e_g - e_g[0]))
+        exc_r = np.max(np.abs(e_r - e_r[0]))
+        assert exc_g <= 1.5 * exc_r + 1e-5, (exc_g, exc_r)
 
 
 def test_sampled_forces_one_million():
