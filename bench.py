@@ -99,6 +99,21 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, n_per_rank, md_steps, max_seconds):
+    """Atom-steps/s of the whole job: every rank advances its own replica."""
+    return world * n_per_rank * md_steps / max_seconds
+
+
 def drift_per_tau(log, dt):
     """Least-squares slope of E_tot/N against time (energy per particle per tau)."""
     e = log["etot_per_n"][:, 0]
@@ -250,16 +265,12 @@ def main():
     clocks.start()
     times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush)
     clk = clocks.stop()
-    total = float(times.sum())
-    if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(float(times.sum()), dist, "cuda")
     info = s.info()
     pairs = s.count_pairs()
     entries = info["list_entries"]
     drift_mixed, fluct_mixed = drift_per_tau(log, wl.DT)
-    value = world * N * CHUNK * args.steps / total
+    value = whole_job_rate(world, N, CHUNK * args.steps, total)
     pair_evals = entries * CHUNK * args.steps * world / total
     flop_step = FLOP_PAIR_IN * 2 * pairs + FLOP_PAIR_OUT * (entries - 2 * pairs)
     launch_s = total / args.steps

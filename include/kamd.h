@@ -228,6 +228,16 @@ md_status md_get_info(md_system* sys, md_info* info);
  * cutoff r < rc_ab, summed over replicas (runs one extra pass). */
 md_status md_count_pairs(md_system* sys, int64_t* pairs_within_cutoff);
 
+/*
+ * md_selftest_barrier: failure-detection self-test of the grid barrier. A
+ * small kernel runs the barrier with one block that never arrives, so the
+ * others' bounded wait runs out after timeout_s (0 < timeout_s <= 60) and they
+ * return. Expected result: MD_ERR_TIMEOUT, with the system's state untouched
+ * and the CUDA context still usable. Any other result means the time limit
+ * does not work. No memory is read or written except the control block.
+ */
+md_status md_selftest_barrier(md_system* sys, double timeout_s);
+
 /* Message for the last failure of this handle (or of md_create when sys is
  * NULL, per host thread). Never NULL. */
 const char* md_last_error(const md_system* sys);

@@ -454,6 +454,8 @@ int list_capacity(const md_system* s) {
   }
   double est = 4.0 / 3.0 * M_PI * rl * rl * rl * dens;
   int cap = (int)std::ceil(1.5 * est + 32);
+  // KAMD_LIST_CAPACITY: start from a given capacity (the list still grows on overflow)
+  if (const char* e = std::getenv("KAMD_LIST_CAPACITY")) cap = std::max(1, std::atoi(e));
   if (cap > nmax - 1) cap = (int)std::max<int64_t>(nmax - 1, 1);
   return cap;
 }
@@ -836,8 +838,8 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   AL(s->d_cellof, nt);
   AL(s->d_scat, nt);
   AL(s->d_nnb, 8 * nt);
-  AL(s->d_part[0], (size_t)s->ntiles * MD_NPART);
-  AL(s->d_part[1], (size_t)s->ntiles * MD_NPART);
+  AL(s->d_part[0], (size_t)s->ntiles * 8 * MD_NPART);
+  AL(s->d_part[1], (size_t)s->ntiles * 8 * MD_NPART);
   AL(s->d_typ_caller, (size_t)ntotal);
   AL(s->d_rep_of_caller, (size_t)ntotal);
   AL(s->d_msd_ref, 3 * (size_t)ntotal);
@@ -1207,6 +1209,43 @@ md_status md_count_pairs(md_system* s, int64_t* pairs) {
   *pairs = (int64_t)(c / 2);
   return MD_OK;
 }
+
+md_status md_selftest_barrier(md_system* s, double timeout_s) {
+  if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
+  if (!(timeout_s > 0) || timeout_s > 60) return fail(s, MD_ERR_INVALID_ARG, "timeout_s must be in (0, 60]");
+  CKS(download_ctl(s));
+  const CtlDev saved = s->ctl;
+  s->ctl.bar_count = 0;
+  s->ctl.pending = 0;
+  CKS(upload_ctl(s));
+  KParams p = make_params(s);
+  p.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+  CK(md_launch_barrier_selftest(p, 4, s->stream));
+  CKS(download_ctl(s));
+  const int pend = s->ctl.pending;
+  // restore the control block so the system stays usable
+  s->ctl = saved;
+  s->ctl.bar_count = 0;
+  CKS(upload_ctl(s));
+  CK(cudaStreamSynchronize(s->stream));
+  if (pend & MD_FLAG_TIMEOUT) return fail(s, MD_ERR_TIMEOUT, "barrier wait ran out as intended (self-test)");
+  return fail(s, MD_ERR_CUDA, "barrier self-test: the wait did not run out");
+}
+
+#ifdef KAMD_PHASE_TIMERS
+// profiling builds only: copy out (and clear) the per-barrier phase timers
+md_status md_debug_phase_times(md_system* s, double* ns, double* cnt) {
+  CKS(download_ctl(s));
+  for (int k = 0; k < 128; ++k) {
+    ns[k] = (double)s->ctl.phase_ns[k];
+    cnt[k] = (double)s->ctl.phase_cnt[k];
+    s->ctl.phase_ns[k] = 0;
+    s->ctl.phase_cnt[k] = 0;
+  }
+  s->ctl.t_last = 0;
+  return upload_ctl(s);
+}
+#endif
 
 const char* md_last_error(const md_system* s) {
   if (!s) return g_create_err.c_str();

@@ -81,6 +81,11 @@ struct CtlDev {
   int64_t steps_done;   // steps completed by the current/last launch
   int err_where;        // phase id where a barrier timed out
   int pad;
+#ifdef KAMD_PHASE_TIMERS
+  unsigned long long t_last;
+  unsigned long long phase_ns[128];
+  unsigned long long phase_cnt[128];
+#endif
 };
 
 struct ThermoDev {  // layout identical to md_thermo
@@ -157,3 +162,4 @@ struct KParams {
 // Host-side launchers (md_kernel.cu).
 cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s);
 cudaError_t md_occupancy(bool mixed, int block, int* blocks_per_sm);
+cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s);

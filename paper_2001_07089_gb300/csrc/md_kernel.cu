@@ -33,7 +33,7 @@
 namespace kamd {
 
 enum { KICK_NONE = 0, KICK_VV = 1, KICK_NH = 2, KICK_NH_EXACT = 3 };
-enum { RED_FORCES = 0, RED_KE = 1, RED_STEP = 2, RED_RESAMPLE = 3 };
+enum { RED_FORCES = 0, RED_KE = 1, RED_STEP = 2, RED_RESAMPLE = 3, RED_STEP_KE = 4 };
 
 struct Shared {
   float4 tabf[MD_MAXTYPES * MD_MAXTYPES];
@@ -55,33 +55,45 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 __device__ __forceinline__ unsigned vload_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
 __device__ __forceinline__ int vload_i32(const int* p) { return *(volatile const int*)p; }
 
-// Grid barrier with a time limit. Returns the pending-flag snapshot taken by
-// the last CTA to arrive (identical for every CTA), or -1 after a timeout.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned x) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned x) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+// Grid barrier with a time limit (acquire/release on the generation word).
+// Returns the pending-flag snapshot taken by the last CTA to arrive
+// (identical for every CTA), or -1 after a timeout.
 __device__ int grid_sync(const KParams& p, Shared& sh, int where) {
   __syncthreads();
   if (threadIdx.x == 0) {
     CtlDev* c = p.ctl;
-    const unsigned g = vload_u32(&c->bar_gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    const unsigned g = ld_acquire_u32(&c->bar_gen);
+    const unsigned arrived = atom_add_acqrel_u32(&c->bar_count, 1u);
     int res = -1;
     if (arrived == gridDim.x - 1) {
       c->bar_count = 0;
       const int pend = atomicOr(&c->pending, 0);
       c->snap[(g + 1) & 1] = pend;
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
+      st_release_u32(&c->bar_gen, g + 1);
       res = pend;
     } else {
       const unsigned long long t0 = globaltimer();
       unsigned it = 0;
       while (true) {
-        if (vload_u32(&c->bar_gen) != g) {
-          __threadfence();
+        if (ld_acquire_u32(&c->bar_gen) != g) {
           res = vload_i32(&c->snap[(g + 1) & 1]);
           break;
         }
-        if (((++it) & 63u) == 0) {
+        if (((++it) & 255u) == 0) {
           if (vload_i32(&c->pending) & MD_FLAG_TIMEOUT) break;
           if (globaltimer() - t0 > p.timeout_ns || it > (1u << 30)) {
             atomicOr(&c->pending, MD_FLAG_TIMEOUT);
@@ -89,10 +101,21 @@ __device__ int grid_sync(const KParams& p, Shared& sh, int where) {
             break;
           }
         }
-        __nanosleep(32);
       }
     }
     sh.snap = res;
+#ifdef KAMD_PHASE_TIMERS
+    // profiling builds only: time between consecutive barriers, charged to
+    // the barrier that closes the phase (block 0's view)
+    if (blockIdx.x == 0 && res >= 0) {
+      const unsigned long long t = globaltimer();
+      if (c->t_last) {
+        c->phase_ns[where & 127] += t - c->t_last;
+        c->phase_cnt[where & 127] += 1;
+      }
+      c->t_last = t;
+    }
+#endif
   }
   __syncthreads();
   return sh.snap;
@@ -253,78 +276,81 @@ __device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bo
 
 // ------------------------------------------------------------------ forces
 
-// Per-tile partial sums (PE, KE, virial, momentum). Every thread of the
-// block calls these. Mixed: float-float warp sums, stored as (hi, lo) pairs.
-// FP64: double warp sums. The T warps of a tile are combined in order.
-__device__ __forceinline__ void tile_partials_ff(Shared& sh, double* part, int tile, bool valid, int T,
-                                                 const float e[6]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* red = reinterpret_cast<float2*>(&sh.red[0][0]);
-  ff w[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) w[k] = warp_sum_ff(ff{e[k], 0.0f});
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) red[warp * MD_NPART + k] = make_float2(w[k].hi, w[k].lo);
+// Pair term for one list entry (mixed path): minimum-image displacement from
+// the signed 32-bit difference of fixed-point top words, then Eq. (KAFix)
+// (force) and Eq. (VshiftedKALJ) (energy) inside the cutoff.
+template <bool ENERGY>
+__device__ __forceinline__ void pair_mix(const Shared& sh, const uint4& pi, const uint4& pj, int tb, float sc,
+                                         float& fx, float& fy, float& fz, float& pe, float& vir) {
+  const float dx = (float)(int)(pi.x - pj.x) * sc;
+  const float dy = (float)(int)(pi.y - pj.y) * sc;
+  const float dz = (float)(int)(pi.z - pj.z) * sc;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const int tt = tb + (int)pj.w;
+  const float4 c = sh.tabf[tt];
+  const float ir2 = __fdividef(1.0f, r2);
+  const float s2 = c.y * ir2;
+  const float s6 = s2 * s2 * s2;
+  const float w = c.z * s6 * (s6 - 0.5f);
+  const bool in = r2 < c.x;
+  const float fr = in ? w * ir2 : 0.0f;
+  fx = fmaf(fr, dx, fx);
+  fy = fmaf(fr, dy, fy);
+  fz = fmaf(fr, dz, fz);
+  if (ENERGY) {
+    pe += in ? fmaf(c.w * s6, s6 - 1.0f, -sh.vshf[tt]) : 0.0f;
+    vir += in ? w : 0.0f;
   }
-  __syncthreads();
-  if (valid && (threadIdx.x % (32 * T)) == 0) {
-    float2* out = reinterpret_cast<float2*>(part) + (int64_t)tile * MD_NPART;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      ff acc = {red[warp * MD_NPART + k].x, red[warp * MD_NPART + k].y};
-      for (int q = 1; q < T; ++q) acc = ff_add(acc, ff{red[(warp + q) * MD_NPART + k].x, red[(warp + q) * MD_NPART + k].y});
-      out[k] = make_float2(acc.hi, acc.lo);
+}
+
+// Walk one lane's column of the list: indices are loaded one batch of 4
+// ahead of the gathers they feed, so list and position latencies overlap.
+template <bool ENERGY>
+__device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __restrict__ pq, const int* lp, int gsz,
+                                             int cnt, const uint4& pi, int tb, float sc, float& fx, float& fy,
+                                             float& fz, float& pe, float& vir) {
+  int q = 0;
+  int j0 = 0, j1 = 0, j2 = 0, j3 = 0;
+  if (cnt >= 4) { j0 = lp[0]; j1 = lp[gsz]; j2 = lp[2 * gsz]; j3 = lp[3 * gsz]; }
+  for (; q + 4 <= cnt; q += 4) {
+    const uint4 p0 = pq[j0], p1 = pq[j1], p2 = pq[j2], p3 = pq[j3];
+    if (q + 8 <= cnt) {
+      const int* nx = lp + (int64_t)(q + 4) * gsz;
+      j0 = nx[0]; j1 = nx[gsz]; j2 = nx[2 * gsz]; j3 = nx[3 * gsz];
     }
+    pair_mix<ENERGY>(sh, pi, p0, tb, sc, fx, fy, fz, pe, vir);
+    pair_mix<ENERGY>(sh, pi, p1, tb, sc, fx, fy, fz, pe, vir);
+    pair_mix<ENERGY>(sh, pi, p2, tb, sc, fx, fy, fz, pe, vir);
+    pair_mix<ENERGY>(sh, pi, p3, tb, sc, fx, fy, fz, pe, vir);
   }
-  __syncthreads();
+  for (; q < cnt; ++q) pair_mix<ENERGY>(sh, pi, pq[lp[(int64_t)q * gsz]], tb, sc, fx, fy, fz, pe, vir);
 }
 
-__device__ __forceinline__ void tile_partials_d(Shared& sh, double* part, int tile, bool valid, int T, double e[6]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) e[k] = warp_sum(e[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sh.red[warp][k] = e[k];
-  }
-  __syncthreads();
-  if (valid && (threadIdx.x % (32 * T)) == 0) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int q = 0; q < T; ++q)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] += sh.red[warp + q][k];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) part[(int64_t)tile * MD_NPART + k] = acc[k];
-  }
-  __syncthreads();
-}
-
-// Force phase. Lane s of particle a walks its own column of the list; the T
-// lanes are combined by a fixed xor tree; lane 0 then applies the velocity
-// rule of `kick`, stores force and velocity, and (if `fuse`) already performs
-// the next position update into the other gather buffer. Without `pairs`
-// only the kinetic partials are formed (forces known, velocities unchanged).
+// Force phase. The work unit is one warp: 32/T particles of one tile with T
+// lanes each (a tile of 32 particles is T units). Lane s of particle a walks
+// its own column of the list; the T lanes are combined by a fixed xor tree;
+// lane 0 then applies the velocity rule of `kick`, stores force and velocity
+// and (if `fuse`) already performs the next position update into the other
+// gather buffer. Without `pairs` only the kinetic partials are formed. Each
+// unit writes its own partial sums, so no CTA-wide synchronisation is needed.
+// `energy` = also form PE and virial (steps whose energies are reported).
 template <bool MIX>
-__device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs) {
+__device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs,
+                            bool energy) {
   const int T = p.T;
   const int gsz = 32 * T;
-  const int tpb = blockDim.x / gsz;
-  const int tib = threadIdx.x / gsz;
-  const int rr = threadIdx.x - tib * gsz;
-  const int a = rr / T, s = rr - a * T;
+  const int lane = threadIdx.x & 31;
+  const int nunits = p.ntiles * T;
   const int64_t nt = p.ntot;
-  for (int base = blockIdx.x * tpb; base < p.ntiles; base += gridDim.x * tpb) {
-    const int tile = base + tib;
-    const bool valid = tile < p.ntiles;
-    const RepDev* R = nullptr;
-    bool act = false;
-    int64_t i = 0;
-    if (valid) {
-      R = &p.reps[p.tile_rep[tile]];
-      act = (tile - R->tile0) * 32 + a < R->n;
-      i = (int64_t)tile * 32 + a;
-    }
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nwarps) {
+    const int tile = u / T;
+    const int w = u - tile * T;
+    const int rr = w * 32 + lane;
+    const int a = rr / T, s = rr - a * T;
+    const RepDev* R = &p.reps[p.tile_rep[tile]];
+    const bool act = (tile - R->tile0) * 32 + a < R->n;
+    const int64_t i = (int64_t)tile * 32 + a;
     const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
     const int cnt = (act && pairs) ? p.nnb[i * T + s] : 0;
     if constexpr (MIX) {
@@ -334,37 +360,17 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         const uint4* __restrict__ pq = p.pq[cur];
         const uint4 pi = pq[i];
         type_i = pi.w;
-        const int tb = (int)pi.w * p.ntypes;
-        const float sc = R->fxs;
-#pragma unroll 4
-        for (int q = 0; q < cnt; ++q) {
-          const int j = lp[q * gsz];
-          const uint4 pj = pq[j];
-          const float dx = (float)(int)(pi.x - pj.x) * sc;
-          const float dy = (float)(int)(pi.y - pj.y) * sc;
-          const float dz = (float)(int)(pi.z - pj.z) * sc;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const int tt = tb + (int)pj.w;
-          const float4 c = sh.tabf[tt];
-          const float ir2 = __fdividef(1.0f, r2);
-          const float s2 = c.y * ir2;
-          const float s6 = s2 * s2 * s2;
-          const float w = c.z * s6 * (s6 - 0.5f);
-          const bool in = r2 < c.x;
-          const float fr = in ? w * ir2 : 0.0f;
-          fx = fmaf(fr, dx, fx);
-          fy = fmaf(fr, dy, fy);
-          fz = fmaf(fr, dz, fz);
-          pe += in ? fmaf(c.w * s6, s6 - 1.0f, -sh.vshf[tt]) : 0.0f;
-          vir += in ? w : 0.0f;
-        }
+        if (energy) lane_sum_mix<true>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
+        else lane_sum_mix<false>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
       }
       for (int o = T >> 1; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
         fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        pe += __shfl_xor_sync(0xffffffffu, pe, o);
-        vir += __shfl_xor_sync(0xffffffffu, vir, o);
+        if (energy) {
+          pe += __shfl_xor_sync(0xffffffffu, pe, o);
+          vir += __shfl_xor_sync(0xffffffffu, vir, o);
+        }
       }
       float e[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (act && s == 0) {
@@ -393,7 +399,12 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[5] = m * v[2];
         if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, type_i);
       }
-      tile_partials_ff(sh, part, tile, valid, T, e);
+      float2* out = reinterpret_cast<float2*>(part) + (int64_t)u * MD_NPART;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const ff t = warp_sum_ff(ff{e[k], 0.0f});
+        if (lane == 0) out[k] = make_float2(t.hi, t.lo);
+      }
     } else {
       double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
       if (act) {
@@ -402,7 +413,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         const int tb = (int)pi.w * p.ntypes;
         const double L = R->L, hL = 0.5 * R->L;
         for (int q = 0; q < cnt; ++q) {
-          const int j = lp[q * gsz];
+          const int j = lp[(int64_t)q * gsz];
           const double4_32a pj = p4[j];
           double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
@@ -457,7 +468,12 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[5] = m * v[2];
         if (fuse) drift_f64(p, *R, i, cur, v, an, 0.0);
       }
-      tile_partials_d(sh, part, tile, valid, T, e);
+      double* out = part + (int64_t)u * MD_NPART;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double t = warp_sum(e[k]);
+        if (lane == 0) out[k] = t;
+      }
     }
   }
 }
@@ -522,45 +538,69 @@ __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* par
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh);
 
-// One warp per replica: fixed-order sum of the replica's tile partials
-// (float-float for the mixed path, double for FP64), then the scalar updates
-// of the mode and, if asked, one thermo record.
+// One CTA per replica: the replica's partial units (upt per tile) are summed
+// thread-strided in fixed order (float-float for the mixed path, double for
+// FP64), then warp trees and the CTA's warps in order; thread 0 applies the
+// scalar updates of the mode and, if asked, writes one thermo record.
 template <bool MIX>
-__device__ void reduce_phase(const KParams& p, const double* part, int mode, int64_t step, bool log_now,
-                             int64_t log_idx) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__device__ void reduce_phase(const KParams& p, Shared& sh, const double* part, int upt, int mode, int64_t step,
+                             bool log_now, int64_t log_idx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const bool nh = (p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT) && p.op == MD_OP_STEPS;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < p.nrep; r += nw) {
+  for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
     RepDev& R = p.reps[r];
+    const int64_t u0 = (int64_t)R.tile0 * upt, nu = (int64_t)R.ntiles * upt;
     double acc[6];
     if constexpr (MIX) {
       ff a[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) a[k] = ff{0.f, 0.f};
       const float2* q0 = reinterpret_cast<const float2*>(part);
-      for (int t = lane; t < R.ntiles; t += 32) {
-        const float2* q = q0 + (int64_t)(R.tile0 + t) * MD_NPART;
+      for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+        const float2* q = q0 + (u0 + t) * MD_NPART;
 #pragma unroll
         for (int k = 0; k < 6; ++k) a[k] = ff_add(a[k], ff{q[k].x, q[k].y});
       }
+      float2* red = reinterpret_cast<float2*>(&sh.red[0][0]);
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         a[k] = warp_sum_ff(a[k]);
-        acc[k] = (double)a[k].hi + (double)a[k].lo;
+        if (lane == 0) red[warp * MD_NPART + k] = make_float2(a[k].hi, a[k].lo);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          ff t = {red[k].x, red[k].y};
+          for (int w = 1; w < nwarp; ++w) t = ff_add(t, ff{red[w * MD_NPART + k].x, red[w * MD_NPART + k].y});
+          acc[k] = (double)t.hi + (double)t.lo;
+        }
       }
     } else {
 #pragma unroll
       for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-      for (int t = lane; t < R.ntiles; t += 32) {
-        const double* q = part + (int64_t)(R.tile0 + t) * MD_NPART;
+      for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+        const double* q = part + (u0 + t) * MD_NPART;
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc[k] += q[k];
       }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+      for (int k = 0; k < 6; ++k) {
+        acc[k] = warp_sum(acc[k]);
+        if (lane == 0) sh.red[warp][k] = acc[k];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          double t = sh.red[0][k];
+          for (int w = 1; w < nwarp; ++w) t += sh.red[w][k];
+          acc[k] = t;
+        }
+      }
     }
-    if (lane == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
+    if (threadIdx.x == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
+    __syncthreads();
   }
 }
 
@@ -583,7 +623,7 @@ __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t
     R.px = acc[3]; R.py = acc[4]; R.pz = acc[5];
     if (nh) {
       const double gnew = (2.0 * R.ke - X * R.T_target) / R.Q;
-      if (mode == RED_STEP) {
+      if (mode == RED_STEP || mode == RED_STEP_KE) {
         R.xi = R.xi + 0.5 * dt * (R.g + gnew);  // Eq. (FoxAndersen_ydottplush)
         R.lns = R.lns_next;
       }
@@ -774,26 +814,25 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
   f = grid_sync(p, sh, 105);
   if (f < 0) return false;
   // B6: Verlet list over the 27 neighbouring cells (or all particles of a
-  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. The T
-  // lanes of a particle split the candidate sequence round-robin; lane s
-  // keeps every candidate whose running index is s mod T, in its own column.
-  const int T = p.T, gsz = 32 * T;
-  const int cap = p.maxrows;
-  for (int64_t idx = gtid; idx < nt * T; idx += stride) {
-    const int64_t i = idx / T;
-    const int s = (int)(idx - i * T);
-    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
-    if (i - R.off >= R.n || !R.doing_rebuild) continue;
-    int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + s;
-    int k = 0, base = 0;
-    int cx = 0, cy = 0, cz = 0;
-    const int nc = R.nc;
-    if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
-    const int ncell_iter = nc > 0 ? 27 : 1;
-    if constexpr (MIX) {
-      const uint4 pi = p.pq[cur][i];
-      const int tb = (int)pi.w * p.ntypes;
-      const float sc = R.fxs;
+  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. One warp
+  // per particle: the lanes test 32 consecutive candidates at a time
+  // (coalesced loads), a ballot compacts the accepted ones in candidate
+  // order, and accepted entry k goes to lane column k mod T, row k / T.
+  {
+    const int T = p.T, gsz = 32 * T;
+    const int cap = p.maxrows * T;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t nwarps = stride >> 5;
+    for (int64_t i = gtid >> 5; i < nt; i += nwarps) {
+      const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+      if (i - R.off >= R.n || !R.doing_rebuild) continue;
+      int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T;
+      int k = 0;
+      int cx = 0, cy = 0, cz = 0;
+      const int nc = R.nc;
+      if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
+      const int ncell_iter = nc > 0 ? 27 : 1;
       for (int cc = 0; cc < ncell_iter; ++cc) {
         int lo, hi;
         if (nc > 0) {
@@ -805,53 +844,44 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
           lo = (int)R.off;
           hi = (int)(R.off + R.n);
         }
-        for (int j = lo + ((s - base % T) + T) % T; j < hi; j += T) {
-          if (j == i) continue;
-          const uint4 pj = p.pq[cur][j];
-          const float dx = (float)(int)(pi.x - pj.x) * sc;
-          const float dy = (float)(int)(pi.y - pj.y) * sc;
-          const float dz = (float)(int)(pi.z - pj.z) * sc;
-          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
-            if (k < cap) lb[(int64_t)k * gsz] = j;
-            ++k;
+        for (int b = lo; b < hi; b += 32) {
+          const int j = b + lane;
+          bool ok = false;
+          if (j < hi && j != i) {
+            if constexpr (MIX) {
+              const uint4 pi = p.pq[cur][i];
+              const uint4 pj = p.pq[cur][j];
+              const float sc = R.fxs;
+              const float dx = (float)(int)(pi.x - pj.x) * sc;
+              const float dy = (float)(int)(pi.y - pj.y) * sc;
+              const float dz = (float)(int)(pi.z - pj.z) * sc;
+              ok = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[(int)pi.w * p.ntypes + (int)pj.w];
+            } else {
+              const double4_32a pi = p.p4[cur][i];
+              const double4_32a pj = p.p4[cur][j];
+              const double L = R.L, hL = 0.5 * R.L;
+              double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+              if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+              if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+              ok = dx * dx + dy * dy + dz * dz < sh.rl2d[(int)pi.w * p.ntypes + (int)pj.w];
+            }
           }
-        }
-        base += hi - lo;
-      }
-      if (s == 0) p.xbq[i] = pi;
-    } else {
-      const double4_32a pi = p.p4[cur][i];
-      const int tb = (int)pi.w * p.ntypes;
-      const double L = R.L, hL = 0.5 * R.L;
-      for (int cc = 0; cc < ncell_iter; ++cc) {
-        int lo, hi;
-        if (nc > 0) {
-          const int ox = cc % 3 - 1, oy = (cc / 3) % 3 - 1, oz = cc / 9 - 1;
-          const int c = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
-          lo = p.cstart[R.cs0 + c];
-          hi = p.cstart[R.cs0 + c + 1];
-        } else {
-          lo = (int)R.off;
-          hi = (int)(R.off + R.n);
-        }
-        for (int j = lo + ((s - base % T) + T) % T; j < hi; j += T) {
-          if (j == i) continue;
-          const double4_32a pj = p.p4[cur][j];
-          double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-          if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
-          if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
-          if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
-          if (dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
-            if (k < cap) lb[(int64_t)k * gsz] = j;
-            ++k;
+          const unsigned m = __ballot_sync(0xffffffffu, ok);
+          if (ok) {
+            const int kk = k + __popc(m & lt_mask);
+            if (kk < cap) lb[(int64_t)(kk / T) * gsz + (kk % T)] = j;
           }
+          k += __popc(m);
         }
-        base += hi - lo;
       }
-      if (s == 0) p.xbd[i] = pi;
+      if (lane < T) p.nnb[i * T + lane] = min(k > lane ? (k - lane + T - 1) / T : 0, p.maxrows);
+      if (lane == 0) {
+        if (k > cap) raise_flag(p, MD_FLAG_OVERFLOW);
+        if constexpr (MIX) p.xbq[i] = p.pq[cur][i];
+        else p.xbd[i] = p.p4[cur][i];
+      }
     }
-    if (k > cap) raise_flag(p, MD_FLAG_OVERFLOW);
-    p.nnb[i * T + s] = min(k, cap);
   }
   f = grid_sync(p, sh, 106);
   if (f < 0) return false;
@@ -909,16 +939,16 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       // then centre and rescale (steps 1-4 of Sec. "Statistical temperature bath")
       resample_draw_phase<MIX>(p, 0, p.part[0]);
       if ((fl = grid_sync(p, sh, 2)) < 0) return;
-      reduce_phase<MIX>(p, p.part[0], RED_RESAMPLE, step0, false, 0);
+      reduce_phase<MIX>(p, sh, p.part[0], 1, RED_RESAMPLE, step0, false, 0);
       if ((fl = grid_sync(p, sh, 3)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, false);
       finish(false, fvalid);
       return;
     }
     const bool pairs = !fvalid || p.op == MD_OP_FORCES;
-    force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs);
+    force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs, true);
     if ((fl = grid_sync(p, sh, 4)) < 0) return;
-    reduce_phase<MIX>(p, p.part[0], pairs ? RED_FORCES : RED_KE, step0, false, 0);
+    reduce_phase<MIX>(p, sh, p.part[0], p.T, pairs ? RED_FORCES : RED_KE, step0, false, 0);
     if ((fl = grid_sync(p, sh, 5)) < 0) return;
     if (p.op == MD_OP_FORCES || p.nsteps == 0) { finish(false, 1); return; }
     drift_phase<MIX>(p, cur, nh, false, true);
@@ -937,14 +967,16 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     const bool rs = p.kind == MD_KIND_RESAMPLE && (step % p.nstep_boltz == 0);
     const bool fuse = !nh && !rs && !last;
     double* part = p.part[step & 1];
-    force_phase<MIX>(p, sh, cur, kick, fuse, part, true);
-    if ((fl = grid_sync(p, sh, 10)) < 0) return;
-    if (fuse) cur ^= 1;
-    now_drifted = fuse;
     const int64_t li = p.log_step0 + s + 1;
     const bool log_now = p.log_every > 0 && (li % p.log_every) == 0 && (li / p.log_every - 1) < p.log_cap;
     const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
-    if (log_now || nh || last || rs) reduce_phase<MIX>(p, part, RED_STEP, step, log_now && !rs, lidx);
+    const bool energy = log_now || last;
+    force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy);
+    if ((fl = grid_sync(p, sh, 10)) < 0) return;
+    if (fuse) cur ^= 1;
+    now_drifted = fuse;
+    if (log_now || nh || last || rs)
+      reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx);
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
@@ -958,7 +990,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       double* part2 = p.part[(step & 1) ^ 1];
       resample_draw_phase<MIX>(p, (uint64_t)(step / p.nstep_boltz), part2);
       if ((fl = grid_sync(p, sh, 14)) < 0) return;
-      reduce_phase<MIX>(p, part2, RED_RESAMPLE, step, log_now, lidx);
+      reduce_phase<MIX>(p, sh, part2, 1, RED_RESAMPLE, step, log_now, lidx);
       if ((fl = grid_sync(p, sh, 15)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, !last);
       if (!last) { cur ^= 1; now_drifted = true; }
@@ -969,7 +1001,21 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
   finish(now_drifted && done < p.nsteps, 1);
 }
 
+// Barrier self-test: block 0 leaves without arriving, so the other blocks'
+// wait runs out after timeout_ns and they raise MD_FLAG_TIMEOUT. Nothing is
+// read or written but the control block.
+__global__ void k_barrier_selftest(KParams p) {
+  __shared__ Shared sh;
+  if (blockIdx.x == 0) return;
+  (void)grid_sync(p, sh, 200);
+}
+
 }  // namespace kamd
+
+cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s) {
+  kamd::k_barrier_selftest<<<blocks, 32, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s) {
   void* args[] = {(void*)&p};

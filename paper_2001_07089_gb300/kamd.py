@@ -32,7 +32,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
 
 EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_set_tuning", "md_get_tuning", "md_autotune",
-            "md_get_info", "md_count_pairs", "md_last_error", "md_destroy")
+            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_last_error", "md_destroy")
 
 
 class md_tuning(ctypes.Structure):
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
             "md_autotune": [P, dbl, i64, ctypes.POINTER(md_tuning), ctypes.POINTER(dbl)],
             "md_get_info": [P, ctypes.POINTER(md_info)],
             "md_count_pairs": [P, ctypes.POINTER(i64)],
+            "md_selftest_barrier": [P, dbl],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -223,6 +224,11 @@ def md_count_pairs(h):
     c = ctypes.c_int64()
     _check(load().md_count_pairs(h, ctypes.byref(c)), h)
     return c.value
+
+
+def md_selftest_barrier(h, timeout_s):
+    """Returns the status code (MD_ERR_TIMEOUT expected) instead of raising."""
+    return load().md_selftest_barrier(h, float(timeout_s))
 
 
 def md_last_error(h=None):
