@@ -125,26 +125,54 @@ def drift_per_tau(log, dt):
     return float(coef[0]), float(np.std(e - A @ coef))
 
 
-def setup_system(kamd, wl, prec, device):
-    L = wl.box_length(N)
-    types = wl.ka_types(N, SEED)
-    s = kamd.System(N, L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
-    s.init_lattice(T_START, 0.05, SEED)
-    s.step_nvt(wl.DT, NVT_STEPS, T_NVT, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
-    return s, L, types
+WORKLOADS = {
+    "ka32k": dict(kind="single", n=32000, seed=2, T0=2.0, T=0.8, setup_nvt=2000, timed="nve",
+                  desc="ka32k: Kob-Andersen 80:20, N=32000, rho=1.2, L=29.876, lattice+0.05 jitter at T=2.0, "
+                       "2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + Verlet list skin 0.3 "
+                       "rebuilt on device; one bench step = 100 MD steps"),
+    "ka1m": dict(kind="single", n=1_000_000, seed=3, T0=0.5, T=0.5, setup_nvt=200, timed="nvt",
+                 desc="ka1m: Kob-Andersen 80:20, N=10^6, rho=1.2, L=94.104, 100^3 lattice+0.05 jitter at T=0.5, "
+                      "Nose-Hoover NVT at T=0.5 dt=0.005 (200 untimed steps, then timed); one bench step = 100 MD steps"),
+    "ensemble": dict(kind="ensemble", nrep=512, seed=4, T0=2.0, setup_nvt=200, timed="nvt",
+                     desc="ensemble: 512 independent KA replicas in one persistent launch, N per replica uniform "
+                          "over {250,500,1000,2000,4000,8000}, rho=1.2, per-replica Nose-Hoover at T uniform in "
+                          "[0.45,2.0], dt=0.005; one bench step = 100 MD steps of every replica"),
+}
 
 
-def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY):
+def setup_system(kamd, wl, prec, device, wk=None):
+    """Build, start and equilibrate the workload's system; returns (system, n_total, T_target)."""
+    wk = wk or WORKLOADS["ka32k"]
+    if wk["kind"] == "single":
+        n = wk["n"]
+        L = wl.box_length(n)
+        types = wl.ka_types(n, wk["seed"])
+        s = kamd.System(n, L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
+        T = np.array([wk["T"]])
+    else:
+        spec = wl.ensemble(wk["nrep"], wk["seed"])
+        s = kamd.System(spec.n, spec.L, np.concatenate(spec.types), wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS,
+                        wl.SKIN, prec)
+        n = spec.total
+        T = spec.T
+    s.init_lattice(wk["T0"], 0.05, wk["seed"])
+    s.step_nvt(wl.DT, wk["setup_nvt"], T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
+    return s, n, T
+
+
+def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY, step=None):
+    """Time `steps` calls of `step(CHUNK, log_every)` (default: NVE) with CUDA events, L2 flushed between."""
+    step = step or (lambda k, le: s.step_nve(dt, k, log_every=le))
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        s.step_nve(dt, CHUNK)
+        step(CHUNK, 0)
     logs, times = [], []
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for k in range(steps):
         flush.zero_()
         ev0[k].record(stream)
-        logs.append(s.step_nve(dt, CHUNK, log_every=log_every))
+        logs.append(step(CHUNK, log_every))
         ev1[k].record(stream)
     torch.cuda.synchronize()
     times = [ev0[k].elapsed_time(ev1[k]) * 1e-3 for k in range(steps)]
@@ -152,20 +180,23 @@ def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY):
     return np.array(times), log
 
 
-def run_e2e(torch, kamd, s, dt, steps):
+def run_e2e(torch, kamd, s, dt, steps, T=None):
     """Public API with host buffers: set_state(host) + step (log to host) + get_state(host)."""
     pos, vel, _ = s.get_state()
     pos = np.ascontiguousarray(pos)
     vel = np.ascontiguousarray(vel)
     img = np.zeros((s.n_total, 3), dtype=np.int32)
     nlog = CHUNK // LOG_EVERY
-    log = np.zeros(nlog, dtype=kamd.THERMO_DTYPE)
+    log = np.zeros(nlog * s.nrep, dtype=kamd.THERMO_DTYPE)
     h = s.handle
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         kamd.md_set_state(h, pos, vel)
-        kamd.md_step_nve(h, dt, CHUNK, log, LOG_EVERY)
+        if T is None:
+            kamd.md_step_nve(h, dt, CHUNK, log, LOG_EVERY)
+        else:
+            kamd.md_step_nvt(h, dt, CHUNK, T, kamd.MD_NVT_NOSE_HOOVER, 100 * dt, 0, log, LOG_EVERY)
         kamd.md_get_state(h, pos, vel, img, 0)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
@@ -228,9 +259,12 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kamd", choices=["kamd", "reference"])
+    ap.add_argument("--workload", default="ka32k", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed bench steps of the all-FP64 arm (default: min(steps, 20) for ka32k, 0 otherwise)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.warmup < 3:
@@ -238,6 +272,7 @@ def main():
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
+    wk = WORKLOADS[args.workload]
 
     import torch
     dist = None
@@ -253,45 +288,55 @@ def main():
     dev = torch.cuda.current_device()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # ---- mixed-precision path (the measured value); every rank runs its own replica
-    s, L, types = setup_system(kamd, wl, "mixed", dev)
+    def stepper(sys_, T):
+        if wk["timed"] == "nve":
+            return lambda k, le: sys_.step_nve(wl.DT, k, log_every=le)
+        return lambda k, le: sys_.step_nvt(wl.DT, k, T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT,
+                                           log_every=le)
+
+    # ---- mixed-precision path (the measured value); every rank runs its own system
+    s, n_sys, T = setup_system(kamd, wl, "mixed", dev, wk)
     tuning = s.tuning
     if not args.no_autotune:
-        tuning, _ = s.autotune(wl.DT, probe_steps=200)
+        tuning, _ = s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 20)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(dev)
     clocks.start()
-    times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush)
+    times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush, step=stepper(s, T))
     clk = clocks.stop()
     total = max_over_ranks(float(times.sum()), dist, "cuda")
     info = s.info()
     pairs = s.count_pairs()
     entries = info["list_entries"]
-    drift_mixed, fluct_mixed = drift_per_tau(log, wl.DT)
-    value = whole_job_rate(world, N, CHUNK * args.steps, total)
+    drift_mixed, fluct_mixed = drift_per_tau(log, wl.DT) if wk["timed"] == "nve" else (None, None)
+    value = whole_job_rate(world, n_sys, CHUNK * args.steps, total)
     pair_evals = entries * CHUNK * args.steps * world / total
     flop_step = FLOP_PAIR_IN * 2 * pairs + FLOP_PAIR_OUT * (entries - 2 * pairs)
     launch_s = total / args.steps
     achieved = flop_step * CHUNK / launch_s / 1e12
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * FP32_LANES_PER_SM * nsm * SM_MAX_MHZ * 1e6 / 1e12
-    e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, max(3, min(args.steps, 20)))
-    e2e_steps = max(3, min(args.steps, 20))
-    e2e_value = world * N * CHUNK * e2e_steps / e2e_el
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(3, min(args.steps, 20))
+        e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, e2e_steps, None if wk["timed"] == "nve" else T)
+        e2e = {"value": world * n_sys * CHUNK * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
     s.close()
 
     # ---- all-FP64 GPU path on the same protocol (context for the mixed number)
     fp64 = None
-    if rank == 0:
-        k64 = args.fp64_steps if args.fp64_steps is not None else max(3, min(args.steps, 20))
-        s64, _, _ = setup_system(kamd, wl, "fp64", dev)
+    k64 = args.fp64_steps if args.fp64_steps is not None else (max(3, min(args.steps, 20))
+                                                                if args.workload == "ka32k" else 0)
+    if rank == 0 and k64 > 0:
+        s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk)
         if not args.no_autotune:
             s64.autotune(wl.DT, probe_steps=50)
-        t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush)
-        d64, f64 = drift_per_tau(log64, wl.DT)
-        fp64 = {"value": N * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
+        t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
+        d64, f64 = drift_per_tau(log64, wl.DT) if wk["timed"] == "nve" else (None, None)
+        fp64 = {"value": n_sys * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
                 "drift_per_particle_per_tau": d64, "etot_fluct_per_particle": f64,
                 "tuning": s64.tuning}
         s64.close()
@@ -306,10 +351,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "ka32k: Kob-Andersen 80:20, N=32000, rho=1.2, L=29.876, lattice+0.05 jitter at "
-                               "T=2.0, 2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + "
-                               "Verlet list skin 0.3 rebuilt on device; one bench step = 100 MD steps",
-                   "n": N, "md_steps_per_bench_step": CHUNK, "timed_md_steps": CHUNK * args.steps,
+        "config": {"workload": wk["desc"], "n": n_sys, "md_steps_per_bench_step": CHUNK,
+                   "timed_md_steps": CHUNK * args.steps,
                    "precision": "mixed: 64-bit fixed-point positions, FP32 velocities/forces/pair math, "
                                 "FP64 reductions",
                    "l2": "flushed between timed steps (256 MB write)", "tuning": tuning,
@@ -325,7 +368,7 @@ def main():
                      "kernel": "md_persistent<mixed> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
     }

@@ -27,6 +27,7 @@ struct md_system {
   int device = 0, nsm = 0;
   int grid = 0;
   int maxrows = 0;
+  int stage_cap = 0;  // candidates the list build stages per cell (dynamic shared memory)
   int64_t ncells = 0;
   bool have_state = false;
   // host mirrors
@@ -56,6 +57,7 @@ struct md_system {
   uint8_t* d_ttyp = nullptr;
   int32_t* d_timg = nullptr;
   int32_t* d_cellof = nullptr;
+  int32_t* d_cell_rep = nullptr;
   int32_t* d_ccount = nullptr;
   int32_t* d_cstart = nullptr;
   int32_t* d_ccursor = nullptr;
@@ -460,13 +462,44 @@ int list_capacity(const md_system* s) {
   return cap;
 }
 
+// Staging area of the list build: the candidates of 27 cells (or of a whole
+// replica too small for cells), with generous headroom over the mean.
+int stage_capacity(const md_system* s) {
+  int cap = 64;
+  for (int r = 0; r < s->nrep; ++r) {
+    const RepDev& R = s->reps[r];
+    const double dens = (double)s->n_per[r] / (R.L * R.L * R.L);
+    int need;
+    if (R.nc > 0) {
+      const double mean = dens * (double)R.cellw * R.cellw * R.cellw;
+      need = (int)std::ceil(27.0 * (1.4 * mean + 12.0));
+    } else {
+      need = (int)s->n_per[r];
+    }
+    cap = std::max(cap, need);
+  }
+  return cap;
+}
+
+size_t stage_bytes(const md_system* s) { return (size_t)s->stage_cap * (s->mixed ? 20 : 36); }
+
 md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   const int T = s->tun.threads_per_atom;
   dfree(s->d_ccount);
   dfree(s->d_cstart);
   dfree(s->d_ccursor);
   dfree(s->d_nbr);
+  dfree(s->d_cell_rep);
   s->maxrows = (cap_entries + T - 1) / T;
+  CKS(dalloc(s, &s->d_cell_rep, (size_t)s->ncells));
+  {
+    std::vector<int32_t> cr((size_t)std::max<int64_t>(s->ncells, 1), 0);
+    for (int r = 0; r < s->nrep; ++r) {
+      const int64_t nc3 = (int64_t)s->reps[r].nc * s->reps[r].nc * s->reps[r].nc;
+      for (int64_t c = 0; c < nc3; ++c) cr[s->reps[r].cell0 + c] = r;
+    }
+    CK(cudaMemcpy(s->d_cell_rep, cr.data(), 4 * cr.size(), cudaMemcpyHostToDevice));
+  }
   CKS(dalloc(s, &s->d_ccount, (size_t)s->ncells));
   CKS(dalloc(s, &s->d_cstart, (size_t)(s->ncells + s->nrep)));
   CKS(dalloc(s, &s->d_ccursor, (size_t)s->ncells));
@@ -488,7 +521,8 @@ md_status mark_rebuild_all(md_system* s) {
 md_status configure_grid(md_system* s) {
   const int b = s->tun.block_size;
   int per_sm = 0;
-  CK(md_occupancy(s->mixed, b, &per_sm));
+  if (stage_bytes(s) > 200 * 1024) return fail(s, MD_ERR_NLIST_OVERFLOW, "list-build staging exceeds shared memory");
+  CK(md_occupancy(s->mixed, b, stage_bytes(s), &per_sm));
   if (per_sm < 1) return fail(s, MD_ERR_INVALID_ARG, "block size too large for the persistent kernel");
   s->grid = per_sm * s->nsm;
   return MD_OK;
@@ -555,6 +589,9 @@ KParams make_params(const md_system* s) {
   p.t_typ = s->d_ttyp;
   p.t_img = s->d_timg;
   p.cellof = s->d_cellof;
+  p.cell_rep = s->d_cell_rep;
+  p.ncells = s->ncells;
+  p.stage_cap = s->stage_cap;
   p.ccount = s->d_ccount;
   p.cstart = s->d_cstart;
   p.ccursor = s->d_ccursor;
@@ -590,7 +627,7 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
     p.log_step0 = done;
     p.log_cap = log_cap;
     p.thermo = s->d_thermo;
-    CK(md_launch_persistent(s->mixed, p, s->grid, s->tun.block_size, s->stream));
+    CK(md_launch_persistent(s->mixed, p, s->grid, s->tun.block_size, stage_bytes(s), s->stream));
     CKS(download_ctl(s));
     if (op == MD_OP_STEPS) done += s->ctl.steps_done;
     const int pend = s->ctl.pending;
@@ -606,8 +643,11 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
       return fail(s, MD_ERR_UNSTABLE, "NaN/Inf state or a particle moved >= L/4 in one step");
     }
     if (pend & MD_FLAG_OVERFLOW) {
+      // a list column or the build's staging area was too small: grow both
       const int cap = s->maxrows * s->tun.threads_per_atom;
       CKS(alloc_cells_and_list(s, cap + cap / 2 + 16));
+      s->stage_cap = std::min(s->stage_cap + s->stage_cap / 2, (int)(200 * 1024 / (s->mixed ? 20 : 36)));
+      CKS(configure_grid(s));
       CKS(mark_rebuild_all(s));
       continue;
     }
@@ -848,6 +888,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   AL(s->d_msd_part, (size_t)s->ntiles * MD_NPART);
   AL(s->d_count, 1);
 #undef AL
+  s->stage_cap = stage_capacity(s);
   st = alloc_cells_and_list(s, list_capacity(s));
   if (st != MD_OK) return destroy_fail(s, st);
   ce = cudaMemcpyAsync(s->d_tile_rep, tile_rep.data(), 4 * tile_rep.size(), cudaMemcpyHostToDevice, s->stream);
@@ -1062,6 +1103,7 @@ md_status md_set_tuning(md_system* s, const md_tuning* t) {
   layout_cells(s);
   for (auto& R : s->reps) R.want_rebuild = 1;
   CKS(upload_reps(s));
+  s->stage_cap = stage_capacity(s);
   CKS(alloc_cells_and_list(s, list_capacity(s)));
   CKS(configure_grid(s));
   CKS(download_ctl(s));
@@ -1261,7 +1303,7 @@ void md_destroy(md_system* s) {
   dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
   dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
   dfree(s->d_timg);
-  dfree(s->d_cellof); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_scat);
+  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_scat);
   dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
   dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
   dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);

@@ -149,6 +149,9 @@ struct KParams {
   int32_t* t_img;
   // cells and list
   int32_t* cellof;
+  int32_t* cell_rep;   // replica of each packed cell
+  int64_t ncells;
+  int stage_cap;       // candidates the list build can stage in dynamic shared memory
   int32_t* ccount;
   int32_t* cstart;
   int32_t* ccursor;
@@ -160,6 +163,6 @@ struct KParams {
 };
 
 // Host-side launchers (md_kernel.cu).
-cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s);
-cudaError_t md_occupancy(bool mixed, int block, int* blocks_per_sm);
+cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm);
 cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s);

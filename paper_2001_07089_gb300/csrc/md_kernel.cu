@@ -336,7 +336,7 @@ __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __re
 // `energy` = also form PE and virial (steps whose energies are reported).
 template <bool MIX>
 __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs,
-                            bool energy) {
+                            bool energy, bool partials = true) {
   const int T = p.T;
   const int gsz = 32 * T;
   const int lane = threadIdx.x & 31;
@@ -348,18 +348,27 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
     const int w = u - tile * T;
     const int rr = w * 32 + lane;
     const int a = rr / T, s = rr - a * T;
-    const RepDev* R = &p.reps[p.tile_rep[tile]];
-    const bool act = (tile - R->tile0) * 32 + a < R->n;
     const int64_t i = (int64_t)tile * 32 + a;
     const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
-    const int cnt = (act && pairs) ? p.nnb[i * T + s] : 0;
     if constexpr (MIX) {
+      // the particle's own data does not depend on its replica: issue these
+      // loads first so that they overlap the replica lookup
+      const uint4 pi = p.pq[cur][i];
+      const int cnt0 = pairs ? p.nnb[i * T + s] : 0;
+      float v[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
+      if (s == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          v[c] = p.velf[c * nt + i];
+          fo[c] = p.frcf[c * nt + i];
+        }
+      }
+      const RepDev* R = &p.reps[p.tile_rep[tile]];
+      const bool act = (tile - R->tile0) * 32 + a < R->n;
+      const int cnt = act ? cnt0 : 0;
       float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, vir = 0.f;
-      uint32_t type_i = 0;
       if (act) {
         const uint4* __restrict__ pq = p.pq[cur];
-        const uint4 pi = pq[i];
-        type_i = pi.w;
         if (energy) lane_sum_mix<true>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
         else lane_sum_mix<false>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
       }
@@ -377,11 +386,11 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         const float im = p.inv_massf, hdt = 0.5f * p.dtf, m = p.massf;
         const float xi = R->xif, xia = R->xiaf;
         const float F[3] = {fx, fy, fz};
-        float v[3], an[3];
+        float an[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float vf = p.velf[c * nt + i];
-          const float ao = p.frcf[c * nt + i] * im;
+          float vf = v[c];
+          const float ao = fo[c] * im;
           const float af = F[c] * im;
           an[c] = af;
           if (kick == KICK_VV) vf = fmaf(hdt, ao + af, vf);
@@ -397,15 +406,20 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[3] = m * v[0];
         e[4] = m * v[1];
         e[5] = m * v[2];
-        if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, type_i);
+        if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, pi.w);
       }
-      float2* out = reinterpret_cast<float2*>(part) + (int64_t)u * MD_NPART;
+      if (partials) {
+        float2* out = reinterpret_cast<float2*>(part) + (int64_t)u * MD_NPART;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const ff t = warp_sum_ff(ff{e[k], 0.0f});
-        if (lane == 0) out[k] = make_float2(t.hi, t.lo);
+        for (int k = 0; k < 6; ++k) {
+          const ff t = warp_sum_ff(ff{e[k], 0.0f});
+          if (lane == 0) out[k] = make_float2(t.hi, t.lo);
+        }
       }
     } else {
+      const RepDev* R = &p.reps[p.tile_rep[tile]];
+      const bool act = (tile - R->tile0) * 32 + a < R->n;
+      const int cnt = (act && pairs) ? p.nnb[i * T + s] : 0;
       double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
       if (act) {
         const double4_32a* __restrict__ p4 = p.p4[cur];
@@ -468,11 +482,13 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[5] = m * v[2];
         if (fuse) drift_f64(p, *R, i, cur, v, an, 0.0);
       }
-      double* out = part + (int64_t)u * MD_NPART;
+      if (partials) {
+        double* out = part + (int64_t)u * MD_NPART;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const double t = warp_sum(e[k]);
-        if (lane == 0) out[k] = t;
+        for (int k = 0; k < 6; ++k) {
+          const double t = warp_sum(e[k]);
+          if (lane == 0) out[k] = t;
+        }
       }
     }
   }
@@ -754,34 +770,51 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
   f = grid_sync(p, sh, 103);
   if (f < 0) return false;
   // B4: rank inside the cell by caller index (deterministic order) and move
-  // every per-particle array to its new slot in the scratch copy
-  for (int64_t k = gtid; k < nt; k += stride) {
-    const RepDev& R = p.reps[p.tile_rep[k >> 5]];
-    if (k - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
-    const int o = p.scat[k];
-    const int c = p.cellof[o];
-    const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
-    const int my = p.gid[o];
-    int rank = 0;
-    for (int q = lo; q < hi; ++q) rank += (p.gid[p.scat[q]] < my);
-    const int64_t d = lo + rank;
-    if constexpr (MIX) {
-      for (int cc = 0; cc < 3; ++cc) {
-        p.t_pfx[cc * nt + d] = p.pfx[cc * nt + o];
-        ((float*)p.t_vel)[cc * nt + d] = p.velf[cc * nt + o];
-        ((float*)p.t_frc)[cc * nt + d] = p.frcf[cc * nt + o];
-        p.t_img[cc * nt + d] = p.img[cc * nt + o];
-      }
-    } else {
-      p.t_p4[d] = p.p4[cur][o];
-      for (int cc = 0; cc < 3; ++cc) {
-        ((double*)p.t_vel)[cc * nt + d] = p.veld[cc * nt + o];
-        ((double*)p.t_frc)[cc * nt + d] = p.frcd[cc * nt + o];
-        p.t_img[cc * nt + d] = p.img[cc * nt + o];
+  // every per-particle array to its new slot in the scratch copy. One warp
+  // per cell: each lane holds one member's caller index and counts, by
+  // shuffles, the members with a smaller one.
+  {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = stride >> 5;
+    for (int64_t gc = gtid >> 5; gc < p.ncells; gc += nwarps) {
+      const RepDev& R = p.reps[p.cell_rep[gc]];
+      if (!R.doing_rebuild || R.nc == 0) continue;
+      const int c = (int)(gc - R.cell0);
+      const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
+      const int n = hi - lo;
+      for (int e0 = 0; e0 < n; e0 += 32) {
+        int o = -1, my = 0x7fffffff;
+        if (e0 + lane < n) {
+          o = p.scat[lo + e0 + lane];
+          my = p.gid[o];
+        }
+        int rank = 0;
+        for (int m0 = 0; m0 < n; m0 += 32) {
+          const int other = (m0 + lane < n) ? p.gid[p.scat[lo + m0 + lane]] : 0x7fffffff;
+          const int lim = min(32, n - m0);
+          for (int t = 0; t < lim; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < my);
+        }
+        if (o < 0) continue;
+        const int64_t d = lo + rank;
+        if constexpr (MIX) {
+          for (int cc = 0; cc < 3; ++cc) {
+            p.t_pfx[cc * nt + d] = p.pfx[cc * nt + o];
+            ((float*)p.t_vel)[cc * nt + d] = p.velf[cc * nt + o];
+            ((float*)p.t_frc)[cc * nt + d] = p.frcf[cc * nt + o];
+            p.t_img[cc * nt + d] = p.img[cc * nt + o];
+          }
+        } else {
+          p.t_p4[d] = p.p4[cur][o];
+          for (int cc = 0; cc < 3; ++cc) {
+            ((double*)p.t_vel)[cc * nt + d] = p.veld[cc * nt + o];
+            ((double*)p.t_frc)[cc * nt + d] = p.frcd[cc * nt + o];
+            p.t_img[cc * nt + d] = p.img[cc * nt + o];
+          }
+        }
+        p.t_gid[d] = p.gid[o];
+        p.t_typ[d] = p.typ[o];
       }
     }
-    p.t_gid[d] = p.gid[o];
-    p.t_typ[d] = p.typ[o];
   }
   f = grid_sync(p, sh, 104);
   if (f < 0) return false;
@@ -814,73 +847,125 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
   f = grid_sync(p, sh, 105);
   if (f < 0) return false;
   // B6: Verlet list over the 27 neighbouring cells (or all particles of a
-  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. One warp
-  // per particle: the lanes test 32 consecutive candidates at a time
-  // (coalesced loads), a ballot compacts the accepted ones in candidate
-  // order, and accepted entry k goes to lane column k mod T, row k / T.
+  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. One CTA
+  // per cell: the candidates of the 27 neighbouring cells are staged in
+  // shared memory (position and slot), then T threads per particle of the
+  // cell scan them, thread s taking every candidate whose index is s mod T
+  // and writing its accepted ones, in candidate order, to list column s.
   {
     const int T = p.T, gsz = 32 * T;
-    const int cap = p.maxrows * T;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t nwarps = stride >> 5;
-    for (int64_t i = gtid >> 5; i < nt; i += nwarps) {
-      const RepDev& R = p.reps[p.tile_rep[i >> 5]];
-      if (i - R.off >= R.n || !R.doing_rebuild) continue;
-      int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T;
-      int k = 0;
-      int cx = 0, cy = 0, cz = 0;
+    const int per_pass = blockDim.x / T;
+    extern __shared__ __align__(32) unsigned char dyn[];
+    const int stage_cap = p.stage_cap;
+    uint4* st_q = reinterpret_cast<uint4*>(dyn);                        // mixed: gather words
+    double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);            // FP64: positions
+    int32_t* st_j = reinterpret_cast<int32_t*>(dyn + (size_t)stage_cap * (MIX ? 16 : 32));
+    __shared__ int s_lo[27], s_hi[27], s_base[28];
+    const int64_t ncell_all = p.ncells + p.nrep;  // cells, then one pseudo-cell per all-pairs replica
+    for (int64_t gc = blockIdx.x; gc < ncell_all; gc += gridDim.x) {
+      int r;
+      int c = 0;
+      if (gc < p.ncells) r = p.cell_rep[gc];
+      else r = (int)(gc - p.ncells);
+      const RepDev& R = p.reps[r];
+      if (!R.doing_rebuild) continue;
+      if (gc < p.ncells) c = (int)(gc - R.cell0);
+      else if (R.nc != 0) continue;
       const int nc = R.nc;
-      if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
-      const int ncell_iter = nc > 0 ? 27 : 1;
-      for (int cc = 0; cc < ncell_iter; ++cc) {
-        int lo, hi;
-        if (nc > 0) {
+      int ilo, ihi, ncand_cells;
+      if (nc > 0) {
+        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+        if (threadIdx.x < 27) {
+          const int cc = threadIdx.x;
           const int ox = cc % 3 - 1, oy = (cc / 3) % 3 - 1, oz = cc / 9 - 1;
-          const int c = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
-          lo = p.cstart[R.cs0 + c];
-          hi = p.cstart[R.cs0 + c + 1];
-        } else {
-          lo = (int)R.off;
-          hi = (int)(R.off + R.n);
+          const int q = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+          s_lo[cc] = p.cstart[R.cs0 + q];
+          s_hi[cc] = p.cstart[R.cs0 + q + 1];
         }
-        for (int b = lo; b < hi; b += 32) {
-          const int j = b + lane;
-          bool ok = false;
-          if (j < hi && j != i) {
-            if constexpr (MIX) {
-              const uint4 pi = p.pq[cur][i];
-              const uint4 pj = p.pq[cur][j];
-              const float sc = R.fxs;
+        ilo = p.cstart[R.cs0 + c];
+        ihi = p.cstart[R.cs0 + c + 1];
+        ncand_cells = 27;
+      } else {
+        if (threadIdx.x == 0) {
+          s_lo[0] = (int)R.off;
+          s_hi[0] = (int)(R.off + R.n);
+        }
+        ilo = (int)R.off;
+        ihi = (int)(R.off + R.n);
+        ncand_cells = 1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int b = 0;
+        for (int cc = 0; cc < ncand_cells; ++cc) {
+          s_base[cc] = b;
+          b += s_hi[cc] - s_lo[cc];
+        }
+        s_base[ncand_cells] = b;
+      }
+      __syncthreads();
+      const int ncand = s_base[ncand_cells];
+      if (ncand > stage_cap) {
+        // more candidates than the staging area holds: flag and skip (the host regrows it)
+        if (threadIdx.x == 0) raise_flag(p, MD_FLAG_OVERFLOW);
+        __syncthreads();
+        continue;
+      }
+      for (int cc = 0; cc < ncand_cells; ++cc) {
+        const int lo = s_lo[cc], n = s_hi[cc] - lo, b = s_base[cc];
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+          if constexpr (MIX) st_q[b + t] = p.pq[cur][lo + t];
+          else st_d[b + t] = p.p4[cur][lo + t];
+          st_j[b + t] = lo + t;
+        }
+      }
+      __syncthreads();
+      for (int i0 = ilo; i0 < ihi; i0 += per_pass) {
+        const int ia = i0 + (int)threadIdx.x / T;
+        const int sl = (int)threadIdx.x % T;
+        if (ia < ihi && (int)threadIdx.x < per_pass * T) {
+          const int64_t i = ia;
+          int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
+          int k = 0;
+          if constexpr (MIX) {
+            const uint4 pi = p.pq[cur][i];
+            const int tb = (int)pi.w * p.ntypes;
+            const float sc = R.fxs;
+            for (int q = sl; q < ncand; q += T) {
+              const uint4 pj = st_q[q];
               const float dx = (float)(int)(pi.x - pj.x) * sc;
               const float dy = (float)(int)(pi.y - pj.y) * sc;
               const float dz = (float)(int)(pi.z - pj.z) * sc;
-              ok = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[(int)pi.w * p.ntypes + (int)pj.w];
-            } else {
-              const double4_32a pi = p.p4[cur][i];
-              const double4_32a pj = p.p4[cur][j];
-              const double L = R.L, hL = 0.5 * R.L;
+              const int j = st_j[q];
+              if (j != i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
+                if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
+                ++k;
+              }
+            }
+            if (sl == 0) p.xbq[i] = pi;
+          } else {
+            const double4_32a pi = p.p4[cur][i];
+            const int tb = (int)pi.w * p.ntypes;
+            const double L = R.L, hL = 0.5 * R.L;
+            for (int q = sl; q < ncand; q += T) {
+              const double4_32a pj = st_d[q];
               double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
               if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
               if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
               if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
-              ok = dx * dx + dy * dy + dz * dz < sh.rl2d[(int)pi.w * p.ntypes + (int)pj.w];
+              const int j = st_j[q];
+              if (j != i && dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
+                if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
+                ++k;
+              }
             }
+            if (sl == 0) p.xbd[i] = pi;
           }
-          const unsigned m = __ballot_sync(0xffffffffu, ok);
-          if (ok) {
-            const int kk = k + __popc(m & lt_mask);
-            if (kk < cap) lb[(int64_t)(kk / T) * gsz + (kk % T)] = j;
-          }
-          k += __popc(m);
+          if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
+          p.nnb[i * T + sl] = min(k, p.maxrows);
         }
       }
-      if (lane < T) p.nnb[i * T + lane] = min(k > lane ? (k - lane + T - 1) / T : 0, p.maxrows);
-      if (lane == 0) {
-        if (k > cap) raise_flag(p, MD_FLAG_OVERFLOW);
-        if constexpr (MIX) p.xbq[i] = p.pq[cur][i];
-        else p.xbd[i] = p.p4[cur][i];
-      }
+      __syncthreads();
     }
   }
   f = grid_sync(p, sh, 106);
@@ -971,12 +1056,12 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     const bool log_now = p.log_every > 0 && (li % p.log_every) == 0 && (li / p.log_every - 1) < p.log_cap;
     const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
     const bool energy = log_now || last;
-    force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy);
+    const bool need_red = log_now || nh || last || rs;
+    force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy, need_red);
     if ((fl = grid_sync(p, sh, 10)) < 0) return;
     if (fuse) cur ^= 1;
     now_drifted = fuse;
-    if (log_now || nh || last || rs)
-      reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx);
+    if (need_red) reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx);
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
@@ -1017,15 +1102,17 @@ cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, cudaStream_t s) {
+cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, size_t smem, cudaStream_t s) {
   void* args[] = {(void*)&p};
-  if (mixed)
-    return cudaLaunchCooperativeKernel((const void*)kamd::md_persistent<true>, dim3(grid), dim3(block), args, 0, s);
-  return cudaLaunchCooperativeKernel((const void*)kamd::md_persistent<false>, dim3(grid), dim3(block), args, 0, s);
+  const void* fn = mixed ? (const void*)kamd::md_persistent<true> : (const void*)kamd::md_persistent<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
 }
 
-cudaError_t md_occupancy(bool mixed, int block, int* blocks_per_sm) {
-  if (mixed)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kamd::md_persistent<true>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kamd::md_persistent<false>, block, 0);
+cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm) {
+  const void* fn = mixed ? (const void*)kamd::md_persistent<true> : (const void*)kamd::md_persistent<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
