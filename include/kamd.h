@@ -238,6 +238,43 @@ md_status md_count_pairs(md_system* sys, int64_t* pairs_within_cutoff);
  */
 md_status md_selftest_barrier(md_system* sys, double timeout_s);
 
+/*
+ * md_forces_noalloc: forces, shifted potential energy and virial of one
+ * configuration, computed without allocating any memory. (The paper has no
+ * counterpart: this is an interface for callers that cannot allocate.)
+ *
+ * Who needs it: code that enqueues work while a stream is being captured
+ * into a CUDA graph (cudaMalloc is not allowed inside a capture), real-time
+ * loops and plugins that must not pay for, or may not trigger, the device
+ * allocator and its implicit synchronisation, and hosts that give the
+ * library a fixed memory budget. Every other caller should use md_forces.
+ *
+ * All scratch lives in one static device array of 1.4 MiB that every GPU
+ * which loads the library holds until the process exits. Hence the limits:
+ * 2 <= n <= 131072 particles and at most 32768 cells (larger boxes use fewer,
+ * larger cells); larger n is rejected with MD_ERR_INVALID_ARG and a message
+ * in md_last_error(NULL).
+ *   pos     device, n*3 doubles (any real values; wrapped into [0, L))
+ *   types   device, n uint8 in [0, ntypes)
+ *   eps, sigma, rc  host tables as in md_create (rc < L/2)
+ *   f       device, n*3 doubles (output, caller order)
+ *   pe, virial  device, one double each (outputs; may be NULL)
+ *   stream  cudaStream_t for all work (NULL: legacy default stream)
+ * Arithmetic is the FP64 path of md_forces (Eqs. (KAFix), (VshiftedKALJ),
+ * minimum image of Sec. "Periodic boundary conditions") over a cell list of
+ * cell edge >= the largest cutoff; results are deterministic.
+ * The call only enqueues work and returns. Its first call on a device (with
+ * that device current) looks up the device address of the static array;
+ * make that first call before any stream capture. Every call on a device
+ * shares the one array, which keeps the previous call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race and give wrong
+ * results; order them.
+ */
+md_status md_forces_noalloc(int64_t n, const double* pos, const uint8_t* types, int ntypes, double L,
+                            const double* eps, const double* sigma, const double* rc,
+                            double* f, double* pe, double* virial, void* stream);
+
 /* Message for the last failure of this handle (or of md_create when sys is
  * NULL, per host thread). Never NULL. */
 const char* md_last_error(const md_system* sys);

@@ -751,6 +751,8 @@ md_status tuning_ok(md_system* s, const md_tuning* t) {
 
 }  // namespace
 
+void kamd_set_global_error(const std::string& msg) { g_create_err = msg; }
+
 // ====================================================================== ABI
 
 extern "C" {

@@ -23,6 +23,7 @@
 // particles is the signed 32-bit difference of their top words, exact.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #define MD_TILE 32
@@ -166,3 +167,5 @@ struct KParams {
 cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm);
 cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s);
+// Message returned by md_last_error(NULL) on this host thread (md_api.cu).
+void kamd_set_global_error(const std::string& msg);

@@ -32,7 +32,8 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
 
 EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_set_tuning", "md_get_tuning", "md_autotune",
-            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_last_error", "md_destroy")
+            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_forces_noalloc", "md_last_error",
+            "md_destroy")
 
 
 class md_tuning(ctypes.Structure):
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
             "md_get_info": [P, ctypes.POINTER(md_info)],
             "md_count_pairs": [P, ctypes.POINTER(i64)],
             "md_selftest_barrier": [P, dbl],
+            "md_forces_noalloc": [i64, P, P, c_int, dbl, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -229,6 +231,14 @@ def md_count_pairs(h):
 def md_selftest_barrier(h, timeout_s):
     """Returns the status code (MD_ERR_TIMEOUT expected) instead of raising."""
     return load().md_selftest_barrier(h, float(timeout_s))
+
+
+def md_forces_noalloc(n, pos, types, ntypes, L, eps, sigma, rc, f, pe=None, virial=None, stream=None):
+    """Device tensors in and out (pos, types, f, pe, virial); host tables. Allocates nothing."""
+    e, s, r = _f64(eps), _f64(sigma), _f64(rc)
+    dp = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+    _check(load().md_forces_noalloc(int(n), dp(pos), dp(types), int(ntypes), float(L), e.ctypes.data, s.ctypes.data,
+                                    r.ctypes.data, dp(f), dp(pe), dp(virial), stream))
 
 
 def md_last_error(h=None):
