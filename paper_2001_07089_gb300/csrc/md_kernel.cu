@@ -769,7 +769,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
   }
   f = grid_sync(p, sh, 103);
   if (f < 0) return false;
-  // B4: rank inside the cell by caller index (deterministic order) and move
+  // B4: rank inside the cell by (type, caller index) (deterministic order) and move
   // every per-particle array to its new slot in the scratch copy. One warp
   // per cell: each lane holds one member's caller index and counts, by
   // shuffles, the members with a smaller one.
@@ -782,15 +782,22 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
       const int c = (int)(gc - R.cell0);
       const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
       const int n = hi - lo;
+      // key = (type, caller index): particles of one species sit together, so
+      // the lanes of a warp walk lists of similar length
       for (int e0 = 0; e0 < n; e0 += 32) {
-        int o = -1, my = 0x7fffffff;
+        int o = -1;
+        unsigned my = 0xffffffffu;
         if (e0 + lane < n) {
           o = p.scat[lo + e0 + lane];
-          my = p.gid[o];
+          my = ((unsigned)p.typ[o] << 30) | (unsigned)p.gid[o];
         }
         int rank = 0;
         for (int m0 = 0; m0 < n; m0 += 32) {
-          const int other = (m0 + lane < n) ? p.gid[p.scat[lo + m0 + lane]] : 0x7fffffff;
+          unsigned other = 0xffffffffu;
+          if (m0 + lane < n) {
+            const int oo = p.scat[lo + m0 + lane];
+            other = ((unsigned)p.typ[oo] << 30) | (unsigned)p.gid[oo];
+          }
           const int lim = min(32, n - m0);
           for (int t = 0; t < lim; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < my);
         }
