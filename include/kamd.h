@@ -91,6 +91,7 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the system */
     int32_t all_pairs_replicas; /* replicas too small for cells (list built by all-pairs scan) */
     int32_t precision;
+    int64_t graph_launches;   /* persistent launches issued as CUDA-graph launches */
 } md_info;
 
 /*

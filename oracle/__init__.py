@@ -221,6 +221,24 @@ def run(pos, vel, types, params: Params, L, dt, nsteps, kind=NVE, T_target=0.0, 
     return {"pos": pos, "vel": vel, "forces": f, "img": img, "state": st, "thermo": thermo[:nlog]}
 
 
+def log_time_grid(n_md, t0=1.0, kmax=60):
+    """Steps of the log-spaced MSD grid (Sec. "Mean square displacement with
+    Python", Eqs. (logtimessteps), (A)), following the paper's loop: walk the
+    time steps, and at each measured step advance t_k by factors of A until
+    round(t_k) moves past it."""
+    A = (float(n_md) / t0) ** (1.0 / float(kmax))
+    t = t0
+    target = int(round(t))
+    out = []
+    for step in range(1, n_md + 1):
+        if target == step:
+            while target == step:
+                t = A * t
+                target = int(round(t))
+            out.append(step)
+    return out
+
+
 def rdf(pos, types, L, dr, nbins):
     pos = _f64(pos, (-1, 3))
     g = np.zeros(3 * nbins)

@@ -81,6 +81,15 @@ struct md_system {
   size_t bytes = 0;
   size_t list_bytes = 0;
   unsigned long long timeout_ns = 10ull * 1000 * 1000 * 1000;
+  // the persistent launch as an instantiated CUDA graph (one cooperative
+  // kernel node whose parameters are updated per call)
+  bool use_graph = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t gnode = nullptr;
+  int g_grid = 0, g_block = 0;
+  size_t g_smem = 0;
+  int64_t graph_launches = 0;
   std::string err;
 };
 
@@ -543,7 +552,9 @@ void fill_tables(const md_system* s, KParams& p) {
     p.rl2_d[t] = rl * rl;
     for (int k = 0; k < 4; ++k) p.tab_f[t][k] = (float)p.tab_d[t][k];
     p.vsh_f[t] = (float)vc;
-    p.rl2_f[t] = (float)(rl * rl);
+    // the mixed list test runs in FP32 on cell-relative coordinates: widen the
+    // radius by a relative 1e-5 so rounding can never drop a pair at the edge
+    p.rl2_f[t] = (float)(rl * rl * (1.0 + 1e-5));
   }
 }
 
@@ -603,14 +614,71 @@ KParams make_params(const md_system* s) {
   return p;
 }
 
+void drop_graph(md_system* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->gexec = nullptr;
+  s->graph = nullptr;
+  s->gnode = nullptr;
+}
+
+// Launch the persistent kernel. By default through an instantiated CUDA graph
+// holding one cooperative kernel node (built once per launch shape, its
+// parameters updated per call); a direct cooperative launch if the graph
+// cannot be built or KAMD_NO_GRAPH is set.
+cudaError_t launch_persistent(md_system* s, const KParams& p) {
+  const size_t smem = stage_bytes(s);
+  const int block = s->tun.block_size;
+  if (s->use_graph) {
+    KParams pc = p;
+    void* args[] = {(void*)&pc};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)md_persistent_fn(s->mixed);
+    kp.gridDim = dim3(s->grid);
+    kp.blockDim = dim3(block);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    cudaError_t e = cudaSuccess;
+    if (!s->gexec || s->g_grid != s->grid || s->g_block != block || s->g_smem != smem) {
+      drop_graph(s);
+      e = cudaFuncSetAttribute(kp.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaGraphCreate(&s->graph, 0);
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(&s->gnode, s->graph, nullptr, 0, &kp);
+      if (e == cudaSuccess) {
+        cudaKernelNodeAttrValue v = {};
+        v.cooperative = 1;
+        e = cudaGraphKernelNodeSetAttribute(s->gnode, cudaKernelNodeAttributeCooperative, &v);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, s->graph, 0);
+      if (e == cudaSuccess) {
+        s->g_grid = s->grid;
+        s->g_block = block;
+        s->g_smem = smem;
+      }
+    } else {
+      e = cudaGraphExecKernelNodeSetParams(s->gexec, s->gnode, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(s->gexec, s->stream);
+    if (e == cudaSuccess) {
+      ++s->graph_launches;
+      return cudaSuccess;
+    }
+    // the driver refused the graph: clear the error and launch directly from now on
+    cudaGetLastError();
+    drop_graph(s);
+    s->use_graph = false;
+  }
+  return md_launch_persistent(s->mixed, p, s->grid, block, smem, s->stream);
+}
+
 // Run the persistent kernel for one operation, growing the neighbour list
 // and relaunching when it overflows. *steps_out receives completed steps.
 md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int64_t nstep_boltz, uint64_t seed,
                  int64_t log_every, int64_t log_cap, int64_t* steps_out) {
   int64_t done = 0;
   for (int attempt = 0; attempt < 8; ++attempt) {
-    // clear the barrier counter and any error flag of an earlier launch
-    CKS(download_ctl(s));
+    // clear the barrier counter and any error flag of an earlier launch (the
+    // host mirror is current: every launch ends with a download of it)
     s->ctl.bar_count = 0;
     s->ctl.pending &= MD_FLAG_REBUILD;
     s->ctl.err_where = 0;
@@ -627,7 +695,7 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
     p.log_step0 = done;
     p.log_cap = log_cap;
     p.thermo = s->d_thermo;
-    CK(md_launch_persistent(s->mixed, p, s->grid, s->tun.block_size, stage_bytes(s), s->stream));
+    CK(launch_persistent(s, p));
     CKS(download_ctl(s));
     if (op == MD_OP_STEPS) done += s->ctl.steps_done;
     const int pend = s->ctl.pending;
@@ -790,6 +858,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
     s->rc[t] = rc[t];
   }
   if (const char* e = std::getenv("KAMD_BARRIER_TIMEOUT_MS")) s->timeout_ns = (unsigned long long)std::atoll(e) * 1000000ull;
+  if (const char* e = std::getenv("KAMD_NO_GRAPH")) s->use_graph = !(e[0] == '1');
   cudaError_t ce = cudaGetDevice(&s->device);
   if (ce != cudaSuccess) return destroy_fail(s, cuda_fail(s, ce, "cudaGetDevice"));
   int major = 0, minor = 0, coop = 0;
@@ -1223,6 +1292,7 @@ md_status md_get_info(md_system* s, md_info* info) {
   info->list_capacity = (int64_t)s->maxrows * s->tun.threads_per_atom;
   info->device_bytes = (int64_t)s->bytes;
   info->precision = s->mixed ? MD_PREC_MIXED : MD_PREC_FP64;
+  info->graph_launches = s->graph_launches;
   return MD_OK;
 }
 
@@ -1299,6 +1369,7 @@ const char* md_last_error(const md_system* s) {
 void md_destroy(md_system* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  drop_graph(s);
   dfree(s->d_reps); dfree(s->d_tile_rep); dfree(s->d_ctl);
   dfree(s->d_pfx); dfree(s->d_pq[0]); dfree(s->d_pq[1]); dfree(s->d_velf); dfree(s->d_frcf); dfree(s->d_xbq);
   dfree(s->d_p4[0]); dfree(s->d_p4[1]); dfree(s->d_veld); dfree(s->d_frcd); dfree(s->d_xbd);

@@ -166,6 +166,7 @@ struct KParams {
 // Host-side launchers (md_kernel.cu).
 cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm);
+const void* md_persistent_fn(bool mixed);
 cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s);
 // Message returned by md_last_error(NULL) on this host thread (md_api.cu).
 void kamd_set_global_error(const std::string& msg);

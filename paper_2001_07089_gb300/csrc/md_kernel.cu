@@ -864,7 +864,6 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
     const int per_pass = blockDim.x / T;
     extern __shared__ __align__(32) unsigned char dyn[];
     const int stage_cap = p.stage_cap;
-    uint4* st_q = reinterpret_cast<uint4*>(dyn);                        // mixed: gather words
     double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);            // FP64: positions
     int32_t* st_j = reinterpret_cast<int32_t*>(dyn + (size_t)stage_cap * (MIX ? 16 : 32));
     __shared__ int s_lo[27], s_hi[27], s_base[28];
@@ -902,6 +901,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
         ncand_cells = 1;
       }
       __syncthreads();
+      if (ilo >= ihi) continue;  // empty cell: no particle needs a list
       if (threadIdx.x == 0) {
         int b = 0;
         for (int cc = 0; cc < ncand_cells; ++cc) {
@@ -918,11 +918,32 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
         __syncthreads();
         continue;
       }
+      // mixed path, boxes of >= 5 cells per edge: stage coordinates relative to
+      // the cell's first particle as FP32 (exact integer differences, converted
+      // once per candidate). There every candidate lies within 2 cells of the
+      // reference and the cell's own particles within 1, so differences of
+      // these relative coordinates are the minimum image (their size stays
+      // below L - r_list); the list test has a whole skin of margin, so FP32
+      // is ample. Smaller boxes stage the fixed-point words and test exactly.
+      const bool rel = nc >= 5;
+      uint4 ref = make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (MIX) ref = p.pq[cur][ilo];
+      float4* st_f = reinterpret_cast<float4*>(dyn);
+      uint4* st_u = reinterpret_cast<uint4*>(dyn);
       for (int cc = 0; cc < ncand_cells; ++cc) {
         const int lo = s_lo[cc], n = s_hi[cc] - lo, b = s_base[cc];
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
-          if constexpr (MIX) st_q[b + t] = p.pq[cur][lo + t];
-          else st_d[b + t] = p.p4[cur][lo + t];
+          if constexpr (MIX) {
+            const uint4 q = p.pq[cur][lo + t];
+            const float sc = R.fxs;
+            if (rel)
+              st_f[b + t] = make_float4((float)(int)(q.x - ref.x) * sc, (float)(int)(q.y - ref.y) * sc,
+                                        (float)(int)(q.z - ref.z) * sc, __int_as_float((int)q.w));
+            else
+              st_u[b + t] = q;
+          } else {
+            st_d[b + t] = p.p4[cur][lo + t];
+          }
           st_j[b + t] = lo + t;
         }
       }
@@ -935,21 +956,39 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
           int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
           int k = 0;
           if constexpr (MIX) {
-            const uint4 pi = p.pq[cur][i];
-            const int tb = (int)pi.w * p.ntypes;
+            const uint4 pq_i = p.pq[cur][i];
             const float sc = R.fxs;
-            for (int q = sl; q < ncand; q += T) {
-              const uint4 pj = st_q[q];
-              const float dx = (float)(int)(pi.x - pj.x) * sc;
-              const float dy = (float)(int)(pi.y - pj.y) * sc;
-              const float dz = (float)(int)(pi.z - pj.z) * sc;
-              const int j = st_j[q];
-              if (j != i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
-                if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
-                ++k;
+            const int tb = (int)pq_i.w * p.ntypes;
+            if (rel) {
+              const float xi = (float)(int)(pq_i.x - ref.x) * sc, yi = (float)(int)(pq_i.y - ref.y) * sc,
+                          zi = (float)(int)(pq_i.z - ref.z) * sc;
+              for (int q = sl; q < ncand; q += T) {
+                const float4 pj = st_f[q];
+                const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + __float_as_int(pj.w)]) {
+                  const int j = st_j[q];
+                  if (j != i) {
+                    if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
+                    ++k;
+                  }
+                }
+              }
+            } else {
+              for (int q = sl; q < ncand; q += T) {
+                const uint4 pj = st_u[q];
+                const float dx = (float)(int)(pq_i.x - pj.x) * sc;
+                const float dy = (float)(int)(pq_i.y - pj.y) * sc;
+                const float dz = (float)(int)(pq_i.z - pj.z) * sc;
+                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
+                  const int j = st_j[q];
+                  if (j != i) {
+                    if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
+                    ++k;
+                  }
+                }
               }
             }
-            if (sl == 0) p.xbq[i] = pi;
+            if (sl == 0) p.xbq[i] = pq_i;
           } else {
             const double4_32a pi = p.p4[cur][i];
             const int tb = (int)pi.w * p.ntypes;
@@ -1115,6 +1154,10 @@ cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int blo
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+const void* md_persistent_fn(bool mixed) {
+  return mixed ? (const void*)kamd::md_persistent<true> : (const void*)kamd::md_persistent<false>;
 }
 
 cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm) {

@@ -44,7 +44,8 @@ class md_info(ctypes.Structure):
     _fields_ = [("n_total", ctypes.c_int64), ("n_replicas", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("steps_done", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
                 ("list_capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("all_pairs_replicas", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("all_pairs_replicas", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("graph_launches", ctypes.c_int64)]
 
 
 class KamdError(RuntimeError):

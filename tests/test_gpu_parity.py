@@ -316,3 +316,24 @@ def test_count_pairs_matches_oracle():
     rc2 = (wl.KA_RC ** 2)[types[:, None], types[None, :]]
     ref = (np.sum(r2 < rc2) - len(pos)) // 2
     assert c == ref
+
+
+def test_graph_launch_matches_direct_launch(monkeypatch):
+    """The persistent kernel launched through its CUDA graph and launched directly give
+    bitwise identical trajectories; the graph path is the one taken by default."""
+    pos, vel, types, L = melted(1000, 95, nsteps=50)
+    runs = []
+    for no_graph in ("0", "1"):
+        monkeypatch.setenv("KAMD_NO_GRAPH", no_graph)
+        with make_system(1000, L, types, "mixed") as s:
+            s.set_state(pos, vel)
+            log = s.step_nvt(0.005, 60, 0.9, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5, log_every=10)
+            log2 = s.step_nve(0.005, 40, log_every=10)
+            st = s.get_state()
+            info = s.info()
+        runs.append((st, log, log2, info))
+    monkeypatch.delenv("KAMD_NO_GRAPH", raising=False)
+    assert runs[0][3]["graph_launches"] >= 2 and runs[1][3]["graph_launches"] == 0
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
