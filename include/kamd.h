@@ -76,7 +76,10 @@ typedef struct {
 typedef struct {
     int threads_per_atom; /* 1, 2, 4 or 8 lanes share one particle's neighbour loop */
     int block_size;       /* 128, 256 or 512 threads per CTA of the persistent kernel */
-    double skin;          /* Verlet skin; list radius r_c,ab + skin; rebuild at skin/2 */
+    double skin;          /* inner list: radius r_c,ab + skin, pruned from the outer list
+                             once any particle moved skin/2 since the last prune */
+    double skin_outer;    /* outer list (> skin): radius r_c,ab + skin_outer, rebuilt with the
+                             cell sort once a particle moved (skin_outer - skin)/2 since */
 } md_tuning;
 
 /* Counters and sizes, for measurement. */
@@ -92,6 +95,7 @@ typedef struct {
     int32_t all_pairs_replicas; /* replicas too small for cells (list built by all-pairs scan) */
     int32_t precision;
     int64_t graph_launches;   /* persistent launches issued as CUDA-graph launches */
+    int64_t prunes;           /* inner-list prune passes */
 } md_info;
 
 /*
@@ -103,7 +107,9 @@ typedef struct {
  *                   (Eqs. (VKALJ), (VshiftedKALJ), (KAFix); Sec. "Periodic
  *                   boundary conditions").
  *   mass    the particle mass (> 0).
- *   skin    Verlet-list skin (>= 0), e.g. 0.3 (LAMMPS "neighbor 0.3 bin").
+ *   skin    Verlet-list skin (>= 0), e.g. 0.3 (LAMMPS "neighbor 0.3 bin"): the
+ *           force list holds pairs within r_c,ab + skin. It is pruned from an
+ *           outer list of skin + 0.4 (md_set_tuning changes both).
  *   prec    MD_PREC_FP64 or MD_PREC_MIXED.
  *   stream  cudaStream_t to enqueue on (NULL: legacy default stream).
  * Positions and velocities start at zero: call md_set_state or md_init_lattice.

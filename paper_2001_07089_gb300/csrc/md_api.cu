@@ -22,7 +22,7 @@ struct md_system {
   std::vector<double> L_per;
   double eps[16] = {0}, sig[16] = {0}, rc[16] = {0};
   double mass = 1.0;
-  md_tuning tun{4, 256, 0.3};
+  md_tuning tun{4, 256, 0.3, 0.7};
   cudaStream_t stream = nullptr;
   int device = 0, nsm = 0;
   int grid = 0;
@@ -42,10 +42,12 @@ struct md_system {
   float* d_velf = nullptr;
   float* d_frcf = nullptr;
   uint4* d_xbq = nullptr;
+  uint4* d_xbq_in = nullptr;
   double4_32a* d_p4[2] = {nullptr, nullptr};
   double* d_veld = nullptr;
   double* d_frcd = nullptr;
   double4_32a* d_xbd = nullptr;
+  double4_32a* d_xbd_in = nullptr;
   int32_t* d_gid = nullptr;
   uint8_t* d_typ = nullptr;
   int32_t* d_img = nullptr;
@@ -63,6 +65,8 @@ struct md_system {
   int32_t* d_ccursor = nullptr;
   int32_t* d_scat = nullptr;
   int32_t* d_nbr = nullptr;
+  int32_t* d_nbr_in = nullptr;
+  int32_t* d_nnb_in = nullptr;
   int32_t* d_nnb = nullptr;
   double* d_part[2] = {nullptr, nullptr};
   uint8_t* d_typ_caller = nullptr;
@@ -439,7 +443,7 @@ double rc_max(const md_system* s) {
 // Cells per edge and list capacity follow from the skin; both are recomputed
 // whenever the tuning changes.
 void layout_cells(md_system* s) {
-  const double rl = rc_max(s) + s->tun.skin;
+  const double rl = rc_max(s) + s->tun.skin_outer;
   int64_t cell0 = 0;
   for (int r = 0; r < s->nrep; ++r) {
     RepDev& R = s->reps[r];
@@ -456,7 +460,7 @@ void layout_cells(md_system* s) {
 }
 
 int list_capacity(const md_system* s) {
-  const double rl = rc_max(s) + s->tun.skin;
+  const double rl = rc_max(s) + s->tun.skin_outer;
   double dens = 0;
   int64_t nmax = 0;
   for (int r = 0; r < s->nrep; ++r) {
@@ -498,6 +502,7 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   dfree(s->d_cstart);
   dfree(s->d_ccursor);
   dfree(s->d_nbr);
+  dfree(s->d_nbr_in);
   dfree(s->d_cell_rep);
   s->maxrows = (cap_entries + T - 1) / T;
   CKS(dalloc(s, &s->d_cell_rep, (size_t)s->ncells));
@@ -514,7 +519,8 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   CKS(dalloc(s, &s->d_ccursor, (size_t)s->ncells));
   const size_t entries = (size_t)s->ntiles * s->maxrows * 32 * T;
   CKS(dalloc(s, &s->d_nbr, entries));
-  s->list_bytes = entries * 4;
+  CKS(dalloc(s, &s->d_nbr_in, entries));
+  s->list_bytes = entries * 8;
   return MD_OK;
 }
 
@@ -543,13 +549,15 @@ void fill_tables(const md_system* s, KParams& p) {
     const double e = s->eps[t], sg = s->sig[t], rc = s->rc[t];
     const double sr6 = std::pow(sg / rc, 6.0);
     const double vc = 4.0 * e * (sr6 * sr6 - sr6);
-    const double rl = rc + s->tun.skin;
+    const double rl = rc + s->tun.skin_outer, rli = rc + s->tun.skin;
     p.tab_d[t][0] = rc * rc;
     p.tab_d[t][1] = sg * sg;
     p.tab_d[t][2] = 48.0 * e;
     p.tab_d[t][3] = 4.0 * e;
     p.vsh_d[t] = vc;
     p.rl2_d[t] = rl * rl;
+    p.rli2_d[t] = rli * rli;
+    p.rli2_f[t] = (float)(rli * rli * (1.0 + 1e-5));
     for (int k = 0; k < 4; ++k) p.tab_f[t][k] = (float)p.tab_d[t][k];
     p.vsh_f[t] = (float)vc;
     // the mixed list test runs in FP32 on cell-relative coordinates: widen the
@@ -570,10 +578,16 @@ KParams make_params(const md_system* s) {
   fill_tables(s, p);
   p.mass = s->mass;
   p.inv_mass = 1.0 / s->mass;
-  p.skin_half2 = 0.25 * s->tun.skin * s->tun.skin;
+  // rebuild the outer list once a particle moved (skin_outer - skin)/2 since
+  // its build (every pair within r_c + skin is then still in it); prune the
+  // inner list once a particle moved skin/2 since the last prune
+  const double so = s->tun.skin_outer, si = s->tun.skin;
+  p.skin_half2 = 0.25 * (so - si) * (so - si);
+  p.prune_half2 = 0.25 * si * si;
   p.massf = (float)s->mass;
   p.inv_massf = (float)(1.0 / s->mass);
   p.skin_half2f = (float)p.skin_half2;
+  p.prune_half2f = (float)p.prune_half2;
   p.timeout_ns = s->timeout_ns;
   p.reps = s->d_reps;
   p.tile_rep = s->d_tile_rep;
@@ -584,11 +598,13 @@ KParams make_params(const md_system* s) {
   p.velf = s->d_velf;
   p.frcf = s->d_frcf;
   p.xbq = s->d_xbq;
+  p.xbq_in = s->d_xbq_in;
   p.p4[0] = s->d_p4[0];
   p.p4[1] = s->d_p4[1];
   p.veld = s->d_veld;
   p.frcd = s->d_frcd;
   p.xbd = s->d_xbd;
+  p.xbd_in = s->d_xbd_in;
   p.gid = s->d_gid;
   p.typ = s->d_typ;
   p.img = s->d_img;
@@ -609,6 +625,8 @@ KParams make_params(const md_system* s) {
   p.scat = s->d_scat;
   p.nbr = s->d_nbr;
   p.nnb = s->d_nnb;
+  p.nbr_in = s->d_nbr_in;
+  p.nnb_in = s->d_nnb_in;
   p.part[0] = s->d_part[0];
   p.part[1] = s->d_part[1];
   return p;
@@ -778,6 +796,7 @@ md_status set_state_impl(md_system* s, const double* pos, const double* vel, int
       s->d_img);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(s->d_nnb, 0, sizeof(int32_t) * 8 * (size_t)s->ntot, s->stream));
+  CK(cudaMemsetAsync(s->d_nnb_in, 0, sizeof(int32_t) * 8 * (size_t)s->ntot, s->stream));
   return after_new_state(s);
 }
 
@@ -812,6 +831,8 @@ md_status tuning_ok(md_system* s, const md_tuning* t) {
   if (!(b == 128 || b == 256 || b == 512)) return fail(s, MD_ERR_INVALID_ARG, "block_size must be 128, 256 or 512");
   if (b < 32 * T) return fail(s, MD_ERR_INVALID_ARG, "block_size must hold at least one 32-particle tile");
   if (!(t->skin >= 0) || !(t->skin < 2.0)) return fail(s, MD_ERR_INVALID_ARG, "skin must be in [0, 2)");
+  if (!(t->skin_outer > t->skin) || !(t->skin_outer < 3.0))
+    return fail(s, MD_ERR_INVALID_ARG, "skin_outer must be in (skin, 3)");
   for (int r = 0; r < s->nrep; ++r)
     if (!(rc_max(s) < 0.5 * s->L_per[r])) return fail(s, MD_ERR_INVALID_ARG, "cutoff must be < L/2");
   return MD_OK;
@@ -852,6 +873,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   s->mixed = prec == MD_PREC_MIXED;
   s->mass = mass;
   s->tun.skin = skin;
+  s->tun.skin_outer = skin + 0.4;
   for (int t = 0; t < ntypes * ntypes; ++t) {
     s->eps[t] = eps[t];
     s->sig[t] = sigma[t];
@@ -919,6 +941,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
     AL(s->d_velf, 3 * nt);
     AL(s->d_frcf, 3 * nt);
     AL(s->d_xbq, nt);
+    AL(s->d_xbq_in, nt);
     AL(s->d_tpfx, 3 * nt);
     float* tv = nullptr;
     float* tf = nullptr;
@@ -932,6 +955,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
     AL(s->d_veld, 3 * nt);
     AL(s->d_frcd, 3 * nt);
     AL(s->d_xbd, nt);
+    AL(s->d_xbd_in, nt);
     AL(s->d_tp4, nt);
     double* tv = nullptr;
     double* tf = nullptr;
@@ -949,6 +973,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   AL(s->d_cellof, nt);
   AL(s->d_scat, nt);
   AL(s->d_nnb, 8 * nt);
+  AL(s->d_nnb_in, 8 * nt);
   AL(s->d_part[0], (size_t)s->ntiles * 8 * MD_NPART);
   AL(s->d_part[1], (size_t)s->ntiles * 8 * MD_NPART);
   AL(s->d_typ_caller, (size_t)ntotal);
@@ -1120,7 +1145,7 @@ md_status md_rdf(md_system* s, double dr, int64_t nbins, double* g, int reset) {
   if (s->ctl.pending & MD_FLAG_REBUILD) CKS(run_op(s, MD_OP_REBUILD, MD_KIND_NVE, 0, 0, 0, 0, 0, 0, nullptr));
   CKS(download_ctl(s));
   const int b = 128;
-  k_rdf<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, (int)nbins, dr, s->tun.skin, s->d_reps, s->d_tile_rep,
+  k_rdf<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, (int)nbins, dr, s->tun.skin_outer, s->d_reps, s->d_tile_rep,
                                                      s->ctl.cur, s->d_pq[s->ctl.cur], s->d_pfx, s->d_p4[s->ctl.cur],
                                                      s->d_typ, s->d_cstart, s->d_rdf);
   CK(cudaGetLastError());
@@ -1206,11 +1231,11 @@ md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* b
   cudaEventCreate(&e1);
   const int Ts[4] = {1, 2, 4, 8};
   const int Bs[3] = {128, 256, 512};
-  const double Ss[3] = {0.2, 0.3, 0.4};
+  const double Ss[6][2] = {{0.2, 0.5}, {0.2, 0.7}, {0.3, 0.6}, {0.3, 0.8}, {0.3, 1.0}, {0.4, 0.9}};
   for (int ti = 0; ti < 4 && st == MD_OK; ++ti)
     for (int bi = 0; bi < 3 && st == MD_OK; ++bi)
-      for (int si = 0; si < 3 && st == MD_OK; ++si) {
-        md_tuning c{Ts[ti], Bs[bi], Ss[si]};
+      for (int si = 0; si < 6 && st == MD_OK; ++si) {
+        md_tuning c{Ts[ti], Bs[bi], Ss[si][0], Ss[si][1]};
         if (c.block_size < 32 * c.threads_per_atom) continue;
         if (tuning_ok(s, &c) != MD_OK) continue;
         st = md_set_tuning(s, &c);
@@ -1293,6 +1318,7 @@ md_status md_get_info(md_system* s, md_info* info) {
   info->device_bytes = (int64_t)s->bytes;
   info->precision = s->mixed ? MD_PREC_MIXED : MD_PREC_FP64;
   info->graph_launches = s->graph_launches;
+  info->prunes = s->ctl.prunes;
   return MD_OK;
 }
 
@@ -1372,6 +1398,7 @@ void md_destroy(md_system* s) {
   drop_graph(s);
   dfree(s->d_reps); dfree(s->d_tile_rep); dfree(s->d_ctl);
   dfree(s->d_pfx); dfree(s->d_pq[0]); dfree(s->d_pq[1]); dfree(s->d_velf); dfree(s->d_frcf); dfree(s->d_xbq);
+  dfree(s->d_xbq_in); dfree(s->d_xbd_in); dfree(s->d_nbr_in); dfree(s->d_nnb_in);
   dfree(s->d_p4[0]); dfree(s->d_p4[1]); dfree(s->d_veld); dfree(s->d_frcd); dfree(s->d_xbd);
   dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
   dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);

@@ -35,6 +35,7 @@
 #define MD_FLAG_OVERFLOW 2
 #define MD_FLAG_UNSTABLE 4
 #define MD_FLAG_TIMEOUT 8
+#define MD_FLAG_PRUNE 16
 
 enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3 };
 enum { MD_KIND_NVE = 0, MD_KIND_NH = 1, MD_KIND_RESAMPLE = 2, MD_KIND_NH_EXACT = 3 };
@@ -80,6 +81,7 @@ struct CtlDev {
   int forces_valid;
   int64_t step;         // global step counter
   int64_t steps_done;   // steps completed by the current/last launch
+  int64_t prunes;       // prune passes since creation
   int err_where;        // phase id where a barrier timed out
   int pad;
 #ifdef KAMD_PHASE_TIMERS
@@ -105,13 +107,16 @@ struct KParams {
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps
   float vsh_f[MD_MAXTYPES * MD_MAXTYPES];      // V(rc)
-  float rl2_f[MD_MAXTYPES * MD_MAXTYPES];      // (rc + skin)^2
+  float rl2_f[MD_MAXTYPES * MD_MAXTYPES];      // outer list radius^2: (rc + skin_outer)^2
+  float rli2_f[MD_MAXTYPES * MD_MAXTYPES];     // inner list radius^2: (rc + skin)^2
   double tab_d[MD_MAXTYPES * MD_MAXTYPES][4];
   double vsh_d[MD_MAXTYPES * MD_MAXTYPES];
   double rl2_d[MD_MAXTYPES * MD_MAXTYPES];
+  double rli2_d[MD_MAXTYPES * MD_MAXTYPES];
   double mass, inv_mass;
-  double skin_half2;   // (skin/2)^2
-  float massf, inv_massf, skin_half2f, dtf;
+  double skin_half2;   // ((skin_outer - skin)/2)^2: move since the outer build that forces a rebuild
+  double prune_half2;  // (skin/2)^2: move since the last prune that forces a prune
+  float massf, inv_massf, skin_half2f, dtf, prune_half2f;
   // operation
   int op;
   int kind;
@@ -132,11 +137,13 @@ struct KParams {
   uint4* pq[2];
   float* velf;
   float* frcf;
-  uint4* xbq;
+  uint4* xbq;          // positions at the last outer build
+  uint4* xbq_in;       // positions at the last prune
   double4_32a* p4[2];
   double* veld;
   double* frcd;
   double4_32a* xbd;
+  double4_32a* xbd_in;
   int32_t* gid;
   uint8_t* typ;
   int32_t* img;
@@ -157,8 +164,10 @@ struct KParams {
   int32_t* cstart;
   int32_t* ccursor;
   int32_t* scat;
-  int32_t* nbr;
+  int32_t* nbr;        // outer list
   int32_t* nnb;
+  int32_t* nbr_in;     // inner (pruned) list, same layout; read by the force phase
+  int32_t* nnb_in;
   // reductions
   double* part[2];     // [ntiles][MD_NPART]: doubles (FP64 path) or float (hi, lo) pairs (mixed path)
 };

@@ -39,9 +39,11 @@ struct Shared {
   float4 tabf[MD_MAXTYPES * MD_MAXTYPES];
   float vshf[MD_MAXTYPES * MD_MAXTYPES];
   float rl2f[MD_MAXTYPES * MD_MAXTYPES];
+  float rli2f[MD_MAXTYPES * MD_MAXTYPES];
   double4_32a tabd[MD_MAXTYPES * MD_MAXTYPES];
   double vshd[MD_MAXTYPES * MD_MAXTYPES];
   double rl2d[MD_MAXTYPES * MD_MAXTYPES];
+  double rli2d[MD_MAXTYPES * MD_MAXTYPES];
   double red[16][MD_NPART];
   int scan[32];
   int snap;
@@ -183,6 +185,9 @@ __device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int
     hi[c] = (uint32_t)(un >> 32);
   }
   p.pq[cur ^ 1][i] = make_uint4(hi[0], hi[1], hi[2], type);
+  // outer list: rebuild once a particle moved more than (skin_outer - skin)/2
+  // since the build; inner list: prune once it moved more than skin/2 since
+  // the last prune
   const uint4 xb = p.xbq[i];
   const float ex = (float)(int)(hi[0] - xb.x) * R.fxs;
   const float ey = (float)(int)(hi[1] - xb.y) * R.fxs;
@@ -191,6 +196,11 @@ __device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int
     p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
     raise_flag(p, MD_FLAG_REBUILD);
   }
+  const uint4 xp = p.xbq_in[i];
+  const float gx = (float)(int)(hi[0] - xp.x) * R.fxs;
+  const float gy = (float)(int)(hi[1] - xp.y) * R.fxs;
+  const float gz = (float)(int)(hi[2] - xp.z) * R.fxs;
+  if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > p.prune_half2f) raise_flag(p, MD_FLAG_PRUNE);
 }
 
 // Position update of one particle, FP64 path: wrap into [0, L).
@@ -228,6 +238,14 @@ __device__ __forceinline__ void drift_f64(const KParams& p, const RepDev& R, int
     p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
     raise_flag(p, MD_FLAG_REBUILD);
   }
+  const double4_32a xp = p.xbd_in[i];
+  double g[3] = {xs[0] - xp.x, xs[1] - xp.y, xs[2] - xp.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (g[c] > 0.5 * R.L) g[c] -= R.L;
+    else if (g[c] < -0.5 * R.L) g[c] += R.L;
+  }
+  if (g[0] * g[0] + g[1] * g[1] + g[2] * g[2] > p.prune_half2) raise_flag(p, MD_FLAG_PRUNE);
 }
 
 // Stand-alone position update for every particle (first step of a call,
@@ -349,12 +367,12 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
     const int rr = w * 32 + lane;
     const int a = rr / T, s = rr - a * T;
     const int64_t i = (int64_t)tile * 32 + a;
-    const int* lp = p.nbr + (int64_t)tile * p.maxrows * gsz + a * T + s;
+    const int* lp = p.nbr_in + (int64_t)tile * p.maxrows * gsz + a * T + s;
     if constexpr (MIX) {
       // the particle's own data does not depend on its replica: issue these
       // loads first so that they overlap the replica lookup
       const uint4 pi = p.pq[cur][i];
-      const int cnt0 = pairs ? p.nnb[i * T + s] : 0;
+      const int cnt0 = pairs ? p.nnb_in[i * T + s] : 0;
       float v[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
       if (s == 0) {
 #pragma unroll
@@ -419,7 +437,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
     } else {
       const RepDev* R = &p.reps[p.tile_rep[tile]];
       const bool act = (tile - R->tile0) * 32 + a < R->n;
-      const int cnt = (act && pairs) ? p.nnb[i * T + s] : 0;
+      const int cnt = (act && pairs) ? p.nnb_in[i * T + s] : 0;
       double fx = 0, fy = 0, fz = 0, pe = 0, vir = 0;
       if (act) {
         const double4_32a* __restrict__ p4 = p.p4[cur];
@@ -491,6 +509,77 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         }
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ prune
+
+// Inner list from the outer one: every lane keeps, in order, the entries of
+// its outer column that now lie within r_c,ab + skin, and the particle's
+// position becomes the reference of the next prune trigger. Runs for every
+// replica (a prune is cheap) whenever any particle has moved skin/2 since the
+// last prune, and after every outer rebuild.
+template <bool MIX>
+__device__ void prune_phase(const KParams& p, Shared& sh, int cur) {
+  const int T = p.T;
+  const int gsz = 32 * T;
+  const int lane = threadIdx.x & 31;
+  const int nunits = p.ntiles * T;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAnd(&p.ctl->pending, ~MD_FLAG_PRUNE);
+    p.ctl->prunes += 1;
+  }
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nwarps) {
+    const int tile = u / T;
+    const int w = u - tile * T;
+    const int rr = w * 32 + lane;
+    const int a = rr / T, s = rr - a * T;
+    const int64_t i = (int64_t)tile * 32 + a;
+    const RepDev& R = p.reps[p.tile_rep[tile]];
+    if ((tile - R.tile0) * 32 + a >= R.n) continue;
+    const int64_t off = (int64_t)tile * p.maxrows * gsz + a * T + s;
+    const int* lo = p.nbr + off;
+    int* li = p.nbr_in + off;
+    const int cnt = p.nnb[i * T + s];
+    int k = 0;
+    if constexpr (MIX) {
+      const uint4* __restrict__ pq = p.pq[cur];
+      const uint4 pi = pq[i];
+      const int tb = (int)pi.w * p.ntypes;
+      const float sc = R.fxs;
+      for (int q = 0; q < cnt; ++q) {
+        const int j = lo[(int64_t)q * gsz];
+        const uint4 pj = pq[j];
+        const float dx = (float)(int)(pi.x - pj.x) * sc;
+        const float dy = (float)(int)(pi.y - pj.y) * sc;
+        const float dz = (float)(int)(pi.z - pj.z) * sc;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj.w]) {
+          li[(int64_t)k * gsz] = j;
+          ++k;
+        }
+      }
+      if (s == 0) p.xbq_in[i] = pi;
+    } else {
+      const double4_32a* __restrict__ p4 = p.p4[cur];
+      const double4_32a pi = p4[i];
+      const int tb = (int)pi.w * p.ntypes;
+      const double L = R.L, hL = 0.5 * R.L;
+      for (int q = 0; q < cnt; ++q) {
+        const int j = lo[(int64_t)q * gsz];
+        const double4_32a pj = p4[j];
+        double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+        if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+        if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+        if (dx * dx + dy * dy + dz * dz < sh.rli2d[tb + (int)pj.w]) {
+          li[(int64_t)k * gsz] = j;
+          ++k;
+        }
+      }
+      if (s == 0) p.xbd_in[i] = pi;
+    }
+    p.nnb_in[i * T + s] = k;
   }
 }
 
@@ -1030,9 +1119,11 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     sh.tabf[t] = make_float4(p.tab_f[t][0], p.tab_f[t][1], p.tab_f[t][2], p.tab_f[t][3]);
     sh.vshf[t] = p.vsh_f[t];
     sh.rl2f[t] = p.rl2_f[t];
+    sh.rli2f[t] = p.rli2_f[t];
     sh.tabd[t] = make_double4_32a(p.tab_d[t][0], p.tab_d[t][1], p.tab_d[t][2], p.tab_d[t][3]);
     sh.vshd[t] = p.vsh_d[t];
     sh.rl2d[t] = p.rl2_d[t];
+    sh.rli2d[t] = p.rli2_d[t];
   }
   CtlDev* C = p.ctl;
   int cur = C->cur;
@@ -1063,6 +1154,11 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if (fl & MD_FLAG_REBUILD) {
       if (!rebuild<MIX>(p, sh, cur, &fl)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(false, fvalid); return; }
+      prune_phase<MIX>(p, sh, cur);
+      if ((fl = grid_sync(p, sh, 107)) < 0) return;
+    } else if (fl & MD_FLAG_PRUNE) {
+      prune_phase<MIX>(p, sh, cur);
+      if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
     if (p.op == MD_OP_REBUILD) { finish(false, fvalid); return; }
     if (p.op == MD_OP_INITVEL) {
@@ -1092,6 +1188,11 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if (fl & MD_FLAG_REBUILD) {
       if (!rebuild<MIX>(p, sh, cur, &fl)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(true, 1); return; }
+      prune_phase<MIX>(p, sh, cur);
+      if ((fl = grid_sync(p, sh, 107)) < 0) return;
+    } else if (fl & MD_FLAG_PRUNE) {
+      prune_phase<MIX>(p, sh, cur);
+      if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
     const int64_t step = step0 + s + 1;
     const bool last = s == p.nsteps - 1;

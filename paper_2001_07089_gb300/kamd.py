@@ -37,7 +37,8 @@ EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_
 
 
 class md_tuning(ctypes.Structure):
-    _fields_ = [("threads_per_atom", ctypes.c_int), ("block_size", ctypes.c_int), ("skin", ctypes.c_double)]
+    _fields_ = [("threads_per_atom", ctypes.c_int), ("block_size", ctypes.c_int), ("skin", ctypes.c_double),
+                ("skin_outer", ctypes.c_double)]
 
 
 class md_info(ctypes.Structure):
@@ -45,7 +46,7 @@ class md_info(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
                 ("list_capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("all_pairs_replicas", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("graph_launches", ctypes.c_int64)]
+                ("graph_launches", ctypes.c_int64), ("prunes", ctypes.c_int64)]
 
 
 class KamdError(RuntimeError):
@@ -199,8 +200,8 @@ def md_msd(h, out, reset_reference):
     _check(load().md_msd(h, out.ctypes.data if out is not None else None, int(reset_reference)), h)
 
 
-def md_set_tuning(h, tpa, block, skin):
-    t = md_tuning(int(tpa), int(block), float(skin))
+def md_set_tuning(h, tpa, block, skin, skin_outer):
+    t = md_tuning(int(tpa), int(block), float(skin), float(skin_outer))
     _check(load().md_set_tuning(h, ctypes.byref(t)), h)
 
 
@@ -345,16 +346,19 @@ class System:
     @property
     def tuning(self):
         t = md_get_tuning(self._h)
-        return {"threads_per_atom": t.threads_per_atom, "block_size": t.block_size, "skin": t.skin}
+        return {"threads_per_atom": t.threads_per_atom, "block_size": t.block_size, "skin": t.skin,
+                "skin_outer": t.skin_outer}
 
-    def set_tuning(self, threads_per_atom=None, block_size=None, skin=None):
+    def set_tuning(self, threads_per_atom=None, block_size=None, skin=None, skin_outer=None):
         cur = self.tuning
-        md_set_tuning(self._h, threads_per_atom or cur["threads_per_atom"], block_size or cur["block_size"],
-                      cur["skin"] if skin is None else skin)
+        sk = cur["skin"] if skin is None else skin
+        so = skin_outer if skin_outer is not None else max(cur["skin_outer"], sk + 0.4)
+        md_set_tuning(self._h, threads_per_atom or cur["threads_per_atom"], block_size or cur["block_size"], sk, so)
 
     def autotune(self, dt, probe_steps=100):
         t, sec = md_autotune(self._h, dt, probe_steps)
-        return {"threads_per_atom": t.threads_per_atom, "block_size": t.block_size, "skin": t.skin}, sec
+        return {"threads_per_atom": t.threads_per_atom, "block_size": t.block_size, "skin": t.skin,
+                "skin_outer": t.skin_outer}, sec
 
     def info(self):
         i = md_get_info(self._h)
