@@ -768,6 +768,8 @@ md_status after_new_state(md_system* s) {
   for (auto& R : s->reps) {
     R.want_rebuild = 1;
     R.xi = R.g = R.lns = R.lns_next = R.xi_a = 0.0;
+    R.xif = R.xiaf = 0.0f;
+    R.prune_epoch = R.rebuild_epoch = -1;
   }
   CKS(upload_reps(s));
   CKS(upload_ctl(s));

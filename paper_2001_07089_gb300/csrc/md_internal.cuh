@@ -67,6 +67,8 @@ struct RepDev {
   float vmeanf[3], vscalef;
   int32_t want_rebuild, doing_rebuild;
   int64_t rebuilds;
+  int64_t prune_epoch;    // force step whose inner list must be pruned first (set by drifts)
+  int64_t rebuild_epoch;  // force step before which the outer list was last rebuilt
   int64_t list_entries;
 };
 

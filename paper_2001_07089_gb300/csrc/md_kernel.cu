@@ -158,7 +158,7 @@ __device__ __forceinline__ void raise_flag(const KParams& p, int f) {
 // coordinate; the wrap is the integer overflow and the image counter follows
 // the carry. Also refreshes the gather copy and checks the half-skin trigger.
 __device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int64_t i, int cur, const float v[3],
-                                          const float a[3], float xi, uint32_t type) {
+                                          const float a[3], float xi, uint32_t type, int64_t nstep) {
   const int64_t nt = p.ntot;
   const float dt = p.dtf, hdt2 = 0.5f * p.dtf * p.dtf;
   float d[3];
@@ -200,12 +200,15 @@ __device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int
   const float gx = (float)(int)(hi[0] - xp.x) * R.fxs;
   const float gy = (float)(int)(hi[1] - xp.y) * R.fxs;
   const float gz = (float)(int)(hi[2] - xp.z) * R.fxs;
-  if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > p.prune_half2f) raise_flag(p, MD_FLAG_PRUNE);
+  if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > p.prune_half2f) {
+    p.reps[p.tile_rep[i >> 5]].prune_epoch = nstep;
+    raise_flag(p, MD_FLAG_PRUNE);
+  }
 }
 
 // Position update of one particle, FP64 path: wrap into [0, L).
 __device__ __forceinline__ void drift_f64(const KParams& p, const RepDev& R, int64_t i, int cur, const double v[3],
-                                          const double a[3], double xi) {
+                                          const double a[3], double xi, int64_t nstep) {
   const int64_t nt = p.ntot;
   const double dt = p.dt, hdt2 = 0.5 * p.dt * p.dt;
   const double4_32a x = p.p4[cur][i];
@@ -245,14 +248,17 @@ __device__ __forceinline__ void drift_f64(const KParams& p, const RepDev& R, int
     if (g[c] > 0.5 * R.L) g[c] -= R.L;
     else if (g[c] < -0.5 * R.L) g[c] += R.L;
   }
-  if (g[0] * g[0] + g[1] * g[1] + g[2] * g[2] > p.prune_half2) raise_flag(p, MD_FLAG_PRUNE);
+  if (g[0] * g[0] + g[1] * g[1] + g[2] * g[2] > p.prune_half2) {
+    p.reps[p.tile_rep[i >> 5]].prune_epoch = nstep;
+    raise_flag(p, MD_FLAG_PRUNE);
+  }
 }
 
 // Stand-alone position update for every particle (first step of a call,
 // Nose-Hoover steps, and the step after a resampling). With `rescale` the
 // velocities are first centred and scaled by the replica's resampling factors.
 template <bool MIX>
-__device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bool drift) {
+__device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bool drift, int64_t nstep) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nt = p.ntot;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += stride) {
@@ -272,7 +278,7 @@ __device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bo
           p.velf[c * nt + i] = v[c];
         }
       }
-      if (drift) drift_mix(p, R, i, cur, v, a, nh ? R.xif : 0.0f, p.pq[cur][i].w);
+      if (drift) drift_mix(p, R, i, cur, v, a, nh ? R.xif : 0.0f, p.pq[cur][i].w, nstep);
     } else {
       double v[3], a[3];
 #pragma unroll
@@ -287,7 +293,7 @@ __device__ void drift_phase(const KParams& p, int cur, bool nh, bool rescale, bo
           p.veld[c * nt + i] = v[c];
         }
       }
-      if (drift) drift_f64(p, R, i, cur, v, a, nh ? R.xi : 0.0);
+      if (drift) drift_f64(p, R, i, cur, v, a, nh ? R.xi : 0.0, nstep);
     }
   }
 }
@@ -354,7 +360,7 @@ __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __re
 // `energy` = also form PE and virial (steps whose energies are reported).
 template <bool MIX>
 __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, bool fuse, double* part, bool pairs,
-                            bool energy, bool partials = true) {
+                            bool energy, bool partials, int64_t nstep) {
   const int T = p.T;
   const int gsz = 32 * T;
   const int lane = threadIdx.x & 31;
@@ -424,7 +430,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[3] = m * v[0];
         e[4] = m * v[1];
         e[5] = m * v[2];
-        if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, pi.w);
+        if (fuse) drift_mix(p, *R, i, cur, v, an, 0.0f, pi.w, nstep);
       }
       if (partials) {
         float2* out = reinterpret_cast<float2*>(part) + (int64_t)u * MD_NPART;
@@ -498,7 +504,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         e[3] = m * v[0];
         e[4] = m * v[1];
         e[5] = m * v[2];
-        if (fuse) drift_f64(p, *R, i, cur, v, an, 0.0);
+        if (fuse) drift_f64(p, *R, i, cur, v, an, 0.0, nstep);
       }
       if (partials) {
         double* out = part + (int64_t)u * MD_NPART;
@@ -516,11 +522,12 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
 
 // Inner list from the outer one: every lane keeps, in order, the entries of
 // its outer column that now lie within r_c,ab + skin, and the particle's
-// position becomes the reference of the next prune trigger. Runs for every
-// replica (a prune is cheap) whenever any particle has moved skin/2 since the
-// last prune, and after every outer rebuild.
+// position becomes the reference of the next prune trigger. A replica is
+// pruned before force step `epoch` if one of its particles asked for it
+// during the drift to that step, or if its outer list was just rebuilt;
+// epochs only grow, so no flag has to be cleared (no race between phases).
 template <bool MIX>
-__device__ void prune_phase(const KParams& p, Shared& sh, int cur) {
+__device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch) {
   const int T = p.T;
   const int gsz = 32 * T;
   const int lane = threadIdx.x & 31;
@@ -538,6 +545,8 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur) {
     const int64_t i = (int64_t)tile * 32 + a;
     const RepDev& R = p.reps[p.tile_rep[tile]];
     if ((tile - R.tile0) * 32 + a >= R.n) continue;
+    // only replicas with a particle past half the inner skin, or a new outer list
+    if (R.prune_epoch != epoch && R.rebuild_epoch != epoch) continue;
     const int64_t off = (int64_t)tile * p.maxrows * gsz + a * T + s;
     const int* lo = p.nbr + off;
     int* li = p.nbr_in + off;
@@ -803,7 +812,7 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
 // Cell sort + Verlet list build for every replica whose want_rebuild is set.
 // Returns false after a barrier timeout. *fl receives the last snapshot.
 template <bool MIX>
-__device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
+__device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t epoch) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nt = p.ntot;
@@ -828,6 +837,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl) {
     if (threadIdx.x == 0) {
       R.want_rebuild = 0;
       R.rebuilds += 1;
+      R.rebuild_epoch = epoch;
     }
     if (R.nc == 0) continue;
     const int ncell = R.nc * R.nc * R.nc;
@@ -1151,13 +1161,14 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
   };
 
   if (!drifted) {
+    // list epochs: the force evaluation at the current positions is "step0"
     if (fl & MD_FLAG_REBUILD) {
-      if (!rebuild<MIX>(p, sh, cur, &fl)) return;
+      if (!rebuild<MIX>(p, sh, cur, &fl, step0)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(false, fvalid); return; }
-      prune_phase<MIX>(p, sh, cur);
+      prune_phase<MIX>(p, sh, cur, step0);
       if ((fl = grid_sync(p, sh, 107)) < 0) return;
     } else if (fl & MD_FLAG_PRUNE) {
-      prune_phase<MIX>(p, sh, cur);
+      prune_phase<MIX>(p, sh, cur, step0);
       if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
     if (p.op == MD_OP_REBUILD) { finish(false, fvalid); return; }
@@ -1168,33 +1179,33 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       if ((fl = grid_sync(p, sh, 2)) < 0) return;
       reduce_phase<MIX>(p, sh, p.part[0], 1, RED_RESAMPLE, step0, false, 0);
       if ((fl = grid_sync(p, sh, 3)) < 0) return;
-      drift_phase<MIX>(p, cur, false, true, false);
+      drift_phase<MIX>(p, cur, false, true, false, step0);
       finish(false, fvalid);
       return;
     }
     const bool pairs = !fvalid || p.op == MD_OP_FORCES;
-    force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs, true);
+    force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs, true, true, step0);
     if ((fl = grid_sync(p, sh, 4)) < 0) return;
     reduce_phase<MIX>(p, sh, p.part[0], p.T, pairs ? RED_FORCES : RED_KE, step0, false, 0);
     if ((fl = grid_sync(p, sh, 5)) < 0) return;
     if (p.op == MD_OP_FORCES || p.nsteps == 0) { finish(false, 1); return; }
-    drift_phase<MIX>(p, cur, nh, false, true);
+    drift_phase<MIX>(p, cur, nh, false, true, step0 + 1);
     cur ^= 1;
     now_drifted = true;
     if ((fl = grid_sync(p, sh, 6)) < 0) return;
   }
   for (int64_t s = 0; s < p.nsteps; ++s) {
     if (fl & MD_FLAG_UNSTABLE) break;
+    const int64_t step = step0 + s + 1;
     if (fl & MD_FLAG_REBUILD) {
-      if (!rebuild<MIX>(p, sh, cur, &fl)) return;
+      if (!rebuild<MIX>(p, sh, cur, &fl, step)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(true, 1); return; }
-      prune_phase<MIX>(p, sh, cur);
+      prune_phase<MIX>(p, sh, cur, step);
       if ((fl = grid_sync(p, sh, 107)) < 0) return;
     } else if (fl & MD_FLAG_PRUNE) {
-      prune_phase<MIX>(p, sh, cur);
+      prune_phase<MIX>(p, sh, cur, step);
       if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
-    const int64_t step = step0 + s + 1;
     const bool last = s == p.nsteps - 1;
     const bool rs = p.kind == MD_KIND_RESAMPLE && (step % p.nstep_boltz == 0);
     const bool fuse = !nh && !rs && !last;
@@ -1204,7 +1215,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
     const bool energy = log_now || last;
     const bool need_red = log_now || nh || last || rs;
-    force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy, need_red);
+    force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy, need_red, step + 1);
     if ((fl = grid_sync(p, sh, 10)) < 0) return;
     if (fuse) cur ^= 1;
     now_drifted = fuse;
@@ -1212,7 +1223,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
-        drift_phase<MIX>(p, cur, true, false, true);
+        drift_phase<MIX>(p, cur, true, false, true, step + 1);
         cur ^= 1;
         now_drifted = true;
         if ((fl = grid_sync(p, sh, 12)) < 0) return;
@@ -1224,7 +1235,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       if ((fl = grid_sync(p, sh, 14)) < 0) return;
       reduce_phase<MIX>(p, sh, part2, 1, RED_RESAMPLE, step, log_now, lidx);
       if ((fl = grid_sync(p, sh, 15)) < 0) return;
-      drift_phase<MIX>(p, cur, false, true, !last);
+      drift_phase<MIX>(p, cur, false, true, !last, step + 1);
       if (!last) { cur ^= 1; now_drifted = true; }
       if ((fl = grid_sync(p, sh, 16)) < 0) return;
     }
