@@ -78,8 +78,10 @@ typedef struct {
     int block_size;       /* 128, 256 or 512 threads per CTA of the persistent kernel */
     double skin;          /* inner list: radius r_c,ab + skin, pruned from the outer list
                              once any particle moved skin/2 since the last prune */
-    double skin_outer;    /* outer list (> skin): radius r_c,ab + skin_outer, rebuilt with the
-                             cell sort once a particle moved (skin_outer - skin)/2 since */
+    double skin_outer;    /* outer list (>= skin): radius r_c,ab + skin_outer, rebuilt with the
+                             cell sort once a particle moved (skin_outer - skin)/2 since;
+                             skin_outer == skin: one list of radius r_c,ab + skin, rebuilt
+                             once a particle moved skin/2, never pruned */
 } md_tuning;
 
 /* Counters and sizes, for measurement. */
@@ -219,8 +221,10 @@ md_status md_set_tuning(md_system* sys, const md_tuning* t);
 md_status md_get_tuning(const md_system* sys, md_tuning* t);
 
 /*
- * md_autotune: time short NVE probes (probe_steps each, dt) over the
- * candidate threads_per_atom x block_size x skin grid and keep the fastest.
+ * md_autotune: time short NVE probes (probe_steps each, dt) and keep the
+ * fastest candidate. Coordinate search: threads_per_atom x block_size at the
+ * current skins, then nine (skin, skin_outer) pairs (three of them one-list)
+ * at the best of those, then threads_per_atom x block_size at the best pair.
  * The system's state is saved before and restored after, so the trajectory
  * is unaffected. best (may be NULL) receives the choice, seconds_per_step (may
  * be NULL) its measured cost.

@@ -580,10 +580,13 @@ KParams make_params(const md_system* s) {
   p.inv_mass = 1.0 / s->mass;
   // rebuild the outer list once a particle moved (skin_outer - skin)/2 since
   // its build (every pair within r_c + skin is then still in it); prune the
-  // inner list once a particle moved skin/2 since the last prune
+  // inner list once a particle moved skin/2 since the last prune. With
+  // skin_outer == skin there is one list: rebuilt at skin/2, never pruned,
+  // and the force phase reads it directly
   const double so = s->tun.skin_outer, si = s->tun.skin;
-  p.skin_half2 = 0.25 * (so - si) * (so - si);
-  p.prune_half2 = 0.25 * si * si;
+  p.dual = so > si ? 1 : 0;
+  p.skin_half2 = p.dual ? 0.25 * (so - si) * (so - si) : 0.25 * si * si;
+  p.prune_half2 = p.dual ? 0.25 * si * si : HUGE_VAL;
   p.massf = (float)s->mass;
   p.inv_massf = (float)(1.0 / s->mass);
   p.skin_half2f = (float)p.skin_half2;
@@ -625,8 +628,8 @@ KParams make_params(const md_system* s) {
   p.scat = s->d_scat;
   p.nbr = s->d_nbr;
   p.nnb = s->d_nnb;
-  p.nbr_in = s->d_nbr_in;
-  p.nnb_in = s->d_nnb_in;
+  p.nbr_in = p.dual ? s->d_nbr_in : s->d_nbr;
+  p.nnb_in = p.dual ? s->d_nnb_in : s->d_nnb;
   p.part[0] = s->d_part[0];
   p.part[1] = s->d_part[1];
   return p;
@@ -833,8 +836,8 @@ md_status tuning_ok(md_system* s, const md_tuning* t) {
   if (!(b == 128 || b == 256 || b == 512)) return fail(s, MD_ERR_INVALID_ARG, "block_size must be 128, 256 or 512");
   if (b < 32 * T) return fail(s, MD_ERR_INVALID_ARG, "block_size must hold at least one 32-particle tile");
   if (!(t->skin >= 0) || !(t->skin < 2.0)) return fail(s, MD_ERR_INVALID_ARG, "skin must be in [0, 2)");
-  if (!(t->skin_outer > t->skin) || !(t->skin_outer < 3.0))
-    return fail(s, MD_ERR_INVALID_ARG, "skin_outer must be in (skin, 3)");
+  if (!(t->skin_outer >= t->skin) || !(t->skin_outer < 3.0))
+    return fail(s, MD_ERR_INVALID_ARG, "skin_outer must be in [skin, 3)");
   for (int r = 0; r < s->nrep; ++r)
     if (!(rc_max(s) < 0.5 * s->L_per[r])) return fail(s, MD_ERR_INVALID_ARG, "cutoff must be < L/2");
   return MD_OK;
@@ -1231,27 +1234,43 @@ md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* b
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // one probe: set the candidate, restart from the saved state, warm up,
+  // then time probe_steps NVE steps
+  auto probe = [&](const md_tuning& c) {
+    if (st != MD_OK) return;
+    if (c.block_size < 32 * c.threads_per_atom) return;
+    if (tuning_ok(s, &c) != MD_OK) return;
+    st = md_set_tuning(s, &c);
+    if (st == MD_OK) st = set_state_impl(s, saved, saved + n3, 1);
+    if (st == MD_OK) st = md_step_nve(s, dt, std::max<int64_t>(probe_steps / 4, 1), nullptr, 0);
+    if (st != MD_OK) return;
+    cudaEventRecord(e0, s->stream);
+    st = md_step_nve(s, dt, probe_steps, nullptr, 0);
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (st == MD_OK && ms < bms) { bms = ms; bt = c; }
+  };
   const int Ts[4] = {1, 2, 4, 8};
   const int Bs[3] = {128, 256, 512};
-  const double Ss[6][2] = {{0.2, 0.5}, {0.2, 0.7}, {0.3, 0.6}, {0.3, 0.8}, {0.3, 1.0}, {0.4, 0.9}};
-  for (int ti = 0; ti < 4 && st == MD_OK; ++ti)
-    for (int bi = 0; bi < 3 && st == MD_OK; ++bi)
-      for (int si = 0; si < 6 && st == MD_OK; ++si) {
-        md_tuning c{Ts[ti], Bs[bi], Ss[si][0], Ss[si][1]};
-        if (c.block_size < 32 * c.threads_per_atom) continue;
-        if (tuning_ok(s, &c) != MD_OK) continue;
-        st = md_set_tuning(s, &c);
-        if (st == MD_OK) st = set_state_impl(s, saved, saved + n3, 1);
-        if (st == MD_OK) st = md_step_nve(s, dt, std::max<int64_t>(probe_steps / 4, 1), nullptr, 0);
-        if (st != MD_OK) break;
-        cudaEventRecord(e0, s->stream);
-        st = md_step_nve(s, dt, probe_steps, nullptr, 0);
-        cudaEventRecord(e1, s->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (st == MD_OK && ms < bms) { bms = ms; bt = c; }
-      }
+  // (skin, skin_outer); equal values mean one list without pruning
+  const double Ss[9][2] = {{0.2, 0.2}, {0.3, 0.3}, {0.4, 0.4}, {0.2, 0.5}, {0.2, 0.7},
+                           {0.3, 0.6}, {0.3, 0.8}, {0.3, 1.0}, {0.4, 0.9}};
+  // coordinate search: lanes x block size at the starting skins, then the
+  // skins at the best of those, then lanes x block size again at the best skins
+  for (int ti = 0; ti < 4; ++ti)
+    for (int bi = 0; bi < 3; ++bi) probe(md_tuning{Ts[ti], Bs[bi], start.skin, start.skin_outer});
+  const md_tuning b1 = bt;
+  for (int si = 0; si < 9; ++si)
+    if (!(Ss[si][0] == start.skin && Ss[si][1] == start.skin_outer))
+      probe(md_tuning{b1.threads_per_atom, b1.block_size, Ss[si][0], Ss[si][1]});
+  const md_tuning b2 = bt;
+  if (!(b2.skin == start.skin && b2.skin_outer == start.skin_outer))
+    for (int ti = 0; ti < 4; ++ti)
+      for (int bi = 0; bi < 3; ++bi)
+        if (!(Ts[ti] == b2.threads_per_atom && Bs[bi] == b2.block_size))
+          probe(md_tuning{Ts[ti], Bs[bi], b2.skin, b2.skin_outer});
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   md_status st2 = md_set_tuning(s, st == MD_OK ? &bt : &start);

@@ -106,6 +106,7 @@ struct KParams {
   int ntiles;
   int T;               // lanes per particle
   int maxrows;         // list rows per tile (capacity per particle = maxrows*T)
+  int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps
   float vsh_f[MD_MAXTYPES * MD_MAXTYPES];      // V(rc)
@@ -116,8 +117,8 @@ struct KParams {
   double rl2_d[MD_MAXTYPES * MD_MAXTYPES];
   double rli2_d[MD_MAXTYPES * MD_MAXTYPES];
   double mass, inv_mass;
-  double skin_half2;   // ((skin_outer - skin)/2)^2: move since the outer build that forces a rebuild
-  double prune_half2;  // (skin/2)^2: move since the last prune that forces a prune
+  double skin_half2;   // ((skin_outer - skin)/2)^2, one list: (skin/2)^2: move since the build that forces a rebuild
+  double prune_half2;  // (skin/2)^2, one list: infinite: move since the last prune that forces a prune
   float massf, inv_massf, skin_half2f, dtf, prune_half2f;
   // operation
   int op;

@@ -196,6 +196,7 @@ __device__ __forceinline__ void drift_mix(const KParams& p, const RepDev& R, int
     p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
     raise_flag(p, MD_FLAG_REBUILD);
   }
+  if (!p.dual) return;
   const uint4 xp = p.xbq_in[i];
   const float gx = (float)(int)(hi[0] - xp.x) * R.fxs;
   const float gy = (float)(int)(hi[1] - xp.y) * R.fxs;
@@ -241,6 +242,7 @@ __device__ __forceinline__ void drift_f64(const KParams& p, const RepDev& R, int
     p.reps[p.tile_rep[i >> 5]].want_rebuild = 1;
     raise_flag(p, MD_FLAG_REBUILD);
   }
+  if (!p.dual) return;
   const double4_32a xp = p.xbd_in[i];
   double g[3] = {xs[0] - xp.x, xs[1] - xp.y, xs[2] - xp.z};
 #pragma unroll
@@ -1165,8 +1167,10 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if (fl & MD_FLAG_REBUILD) {
       if (!rebuild<MIX>(p, sh, cur, &fl, step0)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(false, fvalid); return; }
-      prune_phase<MIX>(p, sh, cur, step0);
-      if ((fl = grid_sync(p, sh, 107)) < 0) return;
+      if (p.dual) {
+        prune_phase<MIX>(p, sh, cur, step0);
+        if ((fl = grid_sync(p, sh, 107)) < 0) return;
+      }
     } else if (fl & MD_FLAG_PRUNE) {
       prune_phase<MIX>(p, sh, cur, step0);
       if ((fl = grid_sync(p, sh, 108)) < 0) return;
@@ -1200,8 +1204,10 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if (fl & MD_FLAG_REBUILD) {
       if (!rebuild<MIX>(p, sh, cur, &fl, step)) return;
       if (fl & MD_FLAG_OVERFLOW) { finish(true, 1); return; }
-      prune_phase<MIX>(p, sh, cur, step);
-      if ((fl = grid_sync(p, sh, 107)) < 0) return;
+      if (p.dual) {
+        prune_phase<MIX>(p, sh, cur, step);
+        if ((fl = grid_sync(p, sh, 107)) < 0) return;
+      }
     } else if (fl & MD_FLAG_PRUNE) {
       prune_phase<MIX>(p, sh, cur, step);
       if ((fl = grid_sync(p, sh, 108)) < 0) return;

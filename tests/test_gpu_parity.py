@@ -245,17 +245,25 @@ def test_batch_replicas_equal_standalone_runs(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_rebuilds_keep_parity_over_long_nve(prec):
-    """400 NVE steps at T=2 cross many list rebuilds. FP64 follows the oracle step by step; the
-    mixed path does for the first 100 steps, after which chaos amplifies FP32 rounding and the
-    comparison is the size of the energy excursions (the conservation statistics)."""
+@pytest.mark.parametrize("skins", [None, (0.3, 0.3), (0.2, 0.5)], ids=["default", "one-list", "dual-0.2-0.5"])
+def test_rebuilds_keep_parity_over_long_nve(prec, skins):
+    """400 NVE steps at T=2 cross many list rebuilds (and inner-list prunes, for two lists).
+    FP64 follows the oracle step by step; the mixed path does for the first 100 steps, after
+    which chaos amplifies FP32 rounding and the comparison is the size of the energy excursions
+    (the conservation statistics)."""
     pos, vel, types, L = melted(1000, 71, nsteps=100)
     ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 400, log_every=1)
     with make_system(1000, L, types, prec) as s:
+        if skins is not None:
+            s.set_tuning(skin=skins[0], skin_outer=skins[1])
         s.set_state(pos, vel)
         log = s.step_nve(0.005, 400, log_every=1)
         info = s.info()
     assert info["rebuilds"] >= 5
+    if skins is not None and skins[0] == skins[1]:
+        assert info["prunes"] == 0
+    else:
+        assert info["prunes"] >= info["rebuilds"]
     if prec == "fp64":
         assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= 1e-9
     else:
