@@ -63,6 +63,9 @@ struct md_system {
   int32_t* d_ccount = nullptr;
   int32_t* d_cstart = nullptr;
   int32_t* d_ccursor = nullptr;
+  int32_t* d_chunk = nullptr;
+  int32_t* d_cta_sm = nullptr;  // SM id per CTA of the persistent grid
+  int cta_sm_cap = 0;
   int32_t* d_scat = nullptr;
   int32_t* d_nbr = nullptr;
   int32_t* d_nbr_in = nullptr;
@@ -494,13 +497,14 @@ int stage_capacity(const md_system* s) {
   return cap;
 }
 
-size_t stage_bytes(const md_system* s) { return (size_t)s->stage_cap * (s->mixed ? 20 : 36); }
+size_t stage_bytes(const md_system* s) { return (size_t)s->stage_cap * (s->mixed ? 16 : 36); }
 
 md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   const int T = s->tun.threads_per_atom;
   dfree(s->d_ccount);
   dfree(s->d_cstart);
   dfree(s->d_ccursor);
+  dfree(s->d_chunk);
   dfree(s->d_nbr);
   dfree(s->d_nbr_in);
   dfree(s->d_cell_rep);
@@ -517,6 +521,7 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   CKS(dalloc(s, &s->d_ccount, (size_t)s->ncells));
   CKS(dalloc(s, &s->d_cstart, (size_t)(s->ncells + s->nrep)));
   CKS(dalloc(s, &s->d_ccursor, (size_t)s->ncells));
+  CKS(dalloc(s, &s->d_chunk, (size_t)(s->ncells / MD_SCAN_CHUNK + 1)));
   const size_t entries = (size_t)s->ntiles * s->maxrows * 32 * T;
   CKS(dalloc(s, &s->d_nbr, entries));
   CKS(dalloc(s, &s->d_nbr_in, entries));
@@ -540,6 +545,13 @@ md_status configure_grid(md_system* s) {
   CK(md_occupancy(s->mixed, b, stage_bytes(s), &per_sm));
   if (per_sm < 1) return fail(s, MD_ERR_INVALID_ARG, "block size too large for the persistent kernel");
   s->grid = per_sm * s->nsm;
+  if (s->grid > s->cta_sm_cap) {
+    dfree(s->d_cta_sm);
+    s->d_cta_sm = nullptr;
+    s->cta_sm_cap = 0;
+    CKS(dalloc(s, &s->d_cta_sm, (size_t)s->grid));
+    s->cta_sm_cap = s->grid;
+  }
   return MD_OK;
 }
 
@@ -625,6 +637,8 @@ KParams make_params(const md_system* s) {
   p.ccount = s->d_ccount;
   p.cstart = s->d_cstart;
   p.ccursor = s->d_ccursor;
+  p.chunk = s->d_chunk;
+  p.cta_sm = s->d_cta_sm;
   p.scat = s->d_scat;
   p.nbr = s->d_nbr;
   p.nnb = s->d_nnb;
@@ -735,7 +749,7 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
       // a list column or the build's staging area was too small: grow both
       const int cap = s->maxrows * s->tun.threads_per_atom;
       CKS(alloc_cells_and_list(s, cap + cap / 2 + 16));
-      s->stage_cap = std::min(s->stage_cap + s->stage_cap / 2, (int)(200 * 1024 / (s->mixed ? 20 : 36)));
+      s->stage_cap = std::min(s->stage_cap + s->stage_cap / 2, (int)(200 * 1024 / (s->mixed ? 16 : 36)));
       CKS(configure_grid(s));
       CKS(mark_rebuild_all(s));
       continue;
@@ -859,13 +873,16 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   if (nrep < 1 || !n_per || !L_per || !types) return fail(nullptr, MD_ERR_INVALID_ARG, "nrep >= 1 and arrays required");
   if (prec != MD_PREC_FP64 && prec != MD_PREC_MIXED) return fail(nullptr, MD_ERR_INVALID_ARG, "unknown precision");
   if (!(mass > 0)) return fail(nullptr, MD_ERR_INVALID_ARG, "mass must be > 0");
-  int64_t ntotal = 0;
+  int64_t ntotal = 0, nslots = 0;
   for (int r = 0; r < nrep; ++r) {
     if (n_per[r] < 2) return fail(nullptr, MD_ERR_INVALID_ARG, "every replica needs n >= 2");
     if (!(L_per[r] > 0) || !std::isfinite(L_per[r])) return fail(nullptr, MD_ERR_INVALID_ARG, "box edge must be > 0");
+    if (n_per[r] >= (int64_t)1 << 30) return fail(nullptr, MD_ERR_INVALID_ARG, "too many particles");
     ntotal += n_per[r];
+    nslots += (n_per[r] + 31) / 32 * 32;
   }
-  if (ntotal > (int64_t)1 << 30) return fail(nullptr, MD_ERR_INVALID_ARG, "at most 2^30 particles");
+  // slot indices share a 32-bit word with a 2-bit type in the list build
+  if (nslots >= (int64_t)1 << 30) return fail(nullptr, MD_ERR_INVALID_ARG, "at most 2^30 - 1 slots (particles padded to tiles of 32 per replica)");
   CKS(validate_table(ntypes, eps, sigma, rc, L_per, nrep, skin));
   for (int64_t g = 0; g < ntotal; ++g)
     if (types[g] >= ntypes) return fail(nullptr, MD_ERR_INVALID_ARG, "type index out of range");
@@ -1424,7 +1441,7 @@ void md_destroy(md_system* s) {
   dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
   dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
   dfree(s->d_timg);
-  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_scat);
+  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_scat);
   dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
   dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
   dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);

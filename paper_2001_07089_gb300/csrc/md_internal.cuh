@@ -28,6 +28,7 @@
 
 #define MD_TILE 32
 #define MD_MAXTYPES 4
+#define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
 
 // pending/commit flag bits (grid-uniform decisions)
@@ -69,6 +70,7 @@ struct RepDev {
   int64_t rebuilds;
   int64_t prune_epoch;    // force step whose inner list must be pruned first (set by drifts)
   int64_t rebuild_epoch;  // force step before which the outer list was last rebuilt
+  int64_t cell_base;      // particles in the cells of earlier replicas that rebuild with this one
   int64_t list_entries;
 };
 
@@ -166,6 +168,8 @@ struct KParams {
   int32_t* ccount;
   int32_t* cstart;
   int32_t* ccursor;
+  int32_t* chunk;      // per-chunk cell-count sums of the cell scan (MD_SCAN_CHUNK cells each)
+  int32_t* cta_sm;     // SM id of each CTA of the current launch
   int32_t* scat;
   int32_t* nbr;        // outer list
   int32_t* nnb;

@@ -47,6 +47,9 @@ struct Shared {
   double red[16][MD_NPART];
   int scan[32];
   int snap;
+  // SM-local work layout of this launch (see sm_layout)
+  unsigned sm_bits[8];
+  int sm_ok, sm_idx, sm_used, sm_cnt, sm_rank;
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -54,6 +57,30 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ int sm_id() {
+  int v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
+}
+
+// Contiguous share [*b, *e) of n items for the SM this CTA runs on, taken by
+// its `per` workers per CTA (warps or the CTA itself) with stride *st.
+// Neighbouring tiles and cells then run on one SM and share its L1. Falls
+// back to a grid-strided split when the layout is unknown.
+__device__ __forceinline__ void sm_share(const Shared& sh, int64_t n, int per, int worker, int64_t* b, int64_t* e,
+                                         int64_t* st) {
+  if (sh.sm_ok) {
+    const int64_t lo = n * sh.sm_idx / sh.sm_used, hi = n * (sh.sm_idx + 1) / sh.sm_used;
+    *b = lo + (int64_t)sh.sm_rank * per + worker;
+    *e = hi;
+    *st = (int64_t)sh.sm_cnt * per;
+  } else {
+    *b = (int64_t)blockIdx.x * per + worker;
+    *e = n;
+    *st = (int64_t)gridDim.x * per;
+  }
+}
+
 __device__ __forceinline__ unsigned vload_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
 __device__ __forceinline__ int vload_i32(const int* p) { return *(volatile const int*)p; }
 
@@ -369,7 +396,9 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
   const int nunits = p.ntiles * T;
   const int64_t nt = p.ntot;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nwarps) {
+  int64_t ub, ue, us;
+  sm_share(sh, nunits, (int)(blockDim.x >> 5), (int)(threadIdx.x >> 5), &ub, &ue, &us);
+  for (int u = (int)ub; u < ue; u += (int)us) {
     const int tile = u / T;
     const int w = u - tile * T;
     const int rr = w * 32 + lane;
@@ -811,165 +840,25 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
   return before;
 }
 
-// Cell sort + Verlet list build for every replica whose want_rebuild is set.
-// Returns false after a barrier timeout. *fl receives the last snapshot.
 template <bool MIX>
-__device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t epoch) {
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t nt = p.ntot;
-  // B1: cell index and count per cell; owners copy want -> doing
-  for (int64_t r = gtid; r < p.nrep; r += stride) p.reps[r].doing_rebuild = p.reps[r].want_rebuild;
-  for (int64_t i = gtid; i < nt; i += stride) {
-    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
-    if (i - R.off >= R.n || !R.want_rebuild || R.nc == 0) continue;
-    int cx, cy, cz;
-    cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
-    const int c = (cz * R.nc + cy) * R.nc + cx;
-    p.cellof[i] = c;
-    atomicAdd(&p.ccount[R.cell0 + c], 1);
-  }
-  int f = grid_sync(p, sh, 101);
-  if (f < 0) return false;
-  // B2: per-replica exclusive scan of the cell counts (one CTA per replica)
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAnd(&p.ctl->pending, ~MD_FLAG_REBUILD);
-  for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
-    RepDev& R = p.reps[r];
-    if (!R.doing_rebuild) continue;
-    if (threadIdx.x == 0) {
-      R.want_rebuild = 0;
-      R.rebuilds += 1;
-      R.rebuild_epoch = epoch;
-    }
-    if (R.nc == 0) continue;
-    const int ncell = R.nc * R.nc * R.nc;
-    const int per = (ncell + blockDim.x - 1) / blockDim.x;
-    const int b0 = min((int)threadIdx.x * per, ncell), b1 = min(b0 + per, ncell);
-    int sum = 0;
-    for (int c = b0; c < b1; ++c) sum += p.ccount[R.cell0 + c];
-    int total;
-    const int pre = block_exclusive_scan(sh, sum, &total);
-    int run = (int)R.off + pre;
-    for (int c = b0; c < b1; ++c) {
-      const int k = p.ccount[R.cell0 + c];
-      p.cstart[R.cs0 + c] = run;
-      p.ccursor[R.cell0 + c] = run;
-      p.ccount[R.cell0 + c] = 0;
-      run += k;
-    }
-    if (threadIdx.x == 0) p.cstart[R.cs0 + ncell] = (int)(R.off + R.n);
-  }
-  f = grid_sync(p, sh, 102);
-  if (f < 0) return false;
-  // B3: scatter slot indices into their cells (order inside a cell arbitrary)
-  for (int64_t i = gtid; i < nt; i += stride) {
-    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
-    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
-    const int slot = atomicAdd(&p.ccursor[R.cell0 + p.cellof[i]], 1);
-    p.scat[slot] = (int)i;
-  }
-  f = grid_sync(p, sh, 103);
-  if (f < 0) return false;
-  // B4: rank inside the cell by (type, caller index) (deterministic order) and move
-  // every per-particle array to its new slot in the scratch copy. One warp
-  // per cell: each lane holds one member's caller index and counts, by
-  // shuffles, the members with a smaller one.
-  {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = stride >> 5;
-    for (int64_t gc = gtid >> 5; gc < p.ncells; gc += nwarps) {
-      const RepDev& R = p.reps[p.cell_rep[gc]];
-      if (!R.doing_rebuild || R.nc == 0) continue;
-      const int c = (int)(gc - R.cell0);
-      const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
-      const int n = hi - lo;
-      // key = (type, caller index): particles of one species sit together, so
-      // the lanes of a warp walk lists of similar length
-      for (int e0 = 0; e0 < n; e0 += 32) {
-        int o = -1;
-        unsigned my = 0xffffffffu;
-        if (e0 + lane < n) {
-          o = p.scat[lo + e0 + lane];
-          my = ((unsigned)p.typ[o] << 30) | (unsigned)p.gid[o];
-        }
-        int rank = 0;
-        for (int m0 = 0; m0 < n; m0 += 32) {
-          unsigned other = 0xffffffffu;
-          if (m0 + lane < n) {
-            const int oo = p.scat[lo + m0 + lane];
-            other = ((unsigned)p.typ[oo] << 30) | (unsigned)p.gid[oo];
-          }
-          const int lim = min(32, n - m0);
-          for (int t = 0; t < lim; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < my);
-        }
-        if (o < 0) continue;
-        const int64_t d = lo + rank;
-        if constexpr (MIX) {
-          for (int cc = 0; cc < 3; ++cc) {
-            p.t_pfx[cc * nt + d] = p.pfx[cc * nt + o];
-            ((float*)p.t_vel)[cc * nt + d] = p.velf[cc * nt + o];
-            ((float*)p.t_frc)[cc * nt + d] = p.frcf[cc * nt + o];
-            p.t_img[cc * nt + d] = p.img[cc * nt + o];
-          }
-        } else {
-          p.t_p4[d] = p.p4[cur][o];
-          for (int cc = 0; cc < 3; ++cc) {
-            ((double*)p.t_vel)[cc * nt + d] = p.veld[cc * nt + o];
-            ((double*)p.t_frc)[cc * nt + d] = p.frcd[cc * nt + o];
-            p.t_img[cc * nt + d] = p.img[cc * nt + o];
-          }
-        }
-        p.t_gid[d] = p.gid[o];
-        p.t_typ[d] = p.typ[o];
-      }
-    }
-  }
-  f = grid_sync(p, sh, 104);
-  if (f < 0) return false;
-  // B5: copy back, refresh the gather copy
-  for (int64_t i = gtid; i < nt; i += stride) {
-    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
-    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
-    if constexpr (MIX) {
-      uint32_t hi[3];
-      for (int cc = 0; cc < 3; ++cc) {
-        const uint64_t u = p.t_pfx[cc * nt + i];
-        p.pfx[cc * nt + i] = u;
-        hi[cc] = (uint32_t)(u >> 32);
-        p.velf[cc * nt + i] = ((const float*)p.t_vel)[cc * nt + i];
-        p.frcf[cc * nt + i] = ((const float*)p.t_frc)[cc * nt + i];
-        p.img[cc * nt + i] = p.t_img[cc * nt + i];
-      }
-      p.pq[cur][i] = make_uint4(hi[0], hi[1], hi[2], p.t_typ[i]);
-    } else {
-      p.p4[cur][i] = p.t_p4[i];
-      for (int cc = 0; cc < 3; ++cc) {
-        p.veld[cc * nt + i] = ((const double*)p.t_vel)[cc * nt + i];
-        p.frcd[cc * nt + i] = ((const double*)p.t_frc)[cc * nt + i];
-        p.img[cc * nt + i] = p.t_img[cc * nt + i];
-      }
-    }
-    p.gid[i] = p.t_gid[i];
-    p.typ[i] = p.t_typ[i];
-  }
-  f = grid_sync(p, sh, 105);
-  if (f < 0) return false;
+__device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cur) {
   // B6: Verlet list over the 27 neighbouring cells (or all particles of a
   // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. One CTA
   // per cell: the candidates of the 27 neighbouring cells are staged in
-  // shared memory (position and slot), then T threads per particle of the
-  // cell scan them, thread s taking every candidate whose index is s mod T
-  // and writing its accepted ones, in candidate order, to list column s.
+  // shared memory (position and slot), then the particles of the cell scan
+  // them, list column s taking every candidate whose index is s mod T, in
+  // candidate order.
   {
     const int T = p.T, gsz = 32 * T;
-    const int per_pass = blockDim.x / T;
     extern __shared__ __align__(32) unsigned char dyn[];
     const int stage_cap = p.stage_cap;
     double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);            // FP64: positions
     int32_t* st_j = reinterpret_cast<int32_t*>(dyn + (size_t)stage_cap * (MIX ? 16 : 32));
     __shared__ int s_lo[27], s_hi[27], s_base[28];
     const int64_t ncell_all = p.ncells + p.nrep;  // cells, then one pseudo-cell per all-pairs replica
-    for (int64_t gc = blockIdx.x; gc < ncell_all; gc += gridDim.x) {
+    int64_t cb, ce, cs;
+    sm_share(sh, ncell_all, 1, 0, &cb, &ce, &cs);
+    for (int64_t gc = cb; gc < ce; gc += cs) {
       int r;
       int c = 0;
       if (gc < p.ncells) r = p.cell_rep[gc];
@@ -1031,90 +920,416 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
       if constexpr (MIX) ref = p.pq[cur][ilo];
       float4* st_f = reinterpret_cast<float4*>(dyn);
       uint4* st_u = reinterpret_cast<uint4*>(dyn);
-      for (int cc = 0; cc < ncand_cells; ++cc) {
-        const int lo = s_lo[cc], n = s_hi[cc] - lo, b = s_base[cc];
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-          if constexpr (MIX) {
-            const uint4 q = p.pq[cur][lo + t];
-            const float sc = R.fxs;
-            if (rel)
-              st_f[b + t] = make_float4((float)(int)(q.x - ref.x) * sc, (float)(int)(q.y - ref.y) * sc,
-                                        (float)(int)(q.z - ref.z) * sc, __int_as_float((int)q.w));
-            else
-              st_u[b + t] = q;
-          } else {
-            st_d[b + t] = p.p4[cur][lo + t];
+      // staging, flattened over all candidates: candidate t belongs to the
+      // staged cell cc with s_base[cc] <= t < s_base[cc + 1] (binary search);
+      // each thread issues its STAGE_U loads before any store
+      {
+        constexpr int STAGE_U = 2;
+        const uint4* __restrict__ pqc = p.pq[cur];
+        const double4_32a* __restrict__ p4c = p.p4[cur];
+        for (int t0 = threadIdx.x; t0 < ncand; t0 += STAGE_U * blockDim.x) {
+          int src[STAGE_U];
+#pragma unroll
+          for (int u = 0; u < STAGE_U; ++u) {
+            const int t = t0 + u * (int)blockDim.x;
+            src[u] = -1;
+            if (t < ncand) {
+              int lo = 0, hi = ncand_cells;
+              while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_base[mid] <= t) lo = mid; else hi = mid;
+              }
+              src[u] = s_lo[lo] + (t - s_base[lo]);
+            }
           }
-          st_j[b + t] = lo + t;
+          if constexpr (MIX) {
+            uint4 q[STAGE_U];
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u)
+              if (src[u] >= 0) q[u] = pqc[src[u]];
+            const float sc = R.fxs;
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u) {
+              if (src[u] < 0) continue;
+              const int t = t0 + u * (int)blockDim.x;
+              // w = (type << 30) | slot: one 16-byte word per candidate
+              const int w = (int)((q[u].w << 30) | (uint32_t)src[u]);
+              if (rel)
+                st_f[t] = make_float4((float)(int)(q[u].x - ref.x) * sc, (float)(int)(q[u].y - ref.y) * sc,
+                                      (float)(int)(q[u].z - ref.z) * sc, __int_as_float(w));
+              else
+                st_u[t] = make_uint4(q[u].x, q[u].y, q[u].z, (uint32_t)w);
+            }
+          } else {
+            double4_32a q[STAGE_U];
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u)
+              if (src[u] >= 0) q[u] = p4c[src[u]];
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u) {
+              if (src[u] < 0) continue;
+              const int t = t0 + u * (int)blockDim.x;
+              st_d[t] = q[u];
+              st_j[t] = src[u];
+            }
+          }
         }
       }
       __syncthreads();
-      for (int i0 = ilo; i0 < ihi; i0 += per_pass) {
-        const int ia = i0 + (int)threadIdx.x / T;
-        const int sl = (int)threadIdx.x % T;
-        if (ia < ihi && (int)threadIdx.x < per_pass * T) {
-          const int64_t i = ia;
+      // scan: column s of particle a takes candidates s, s + T, s + 2T, ... in
+      // order. m lanes of one warp (m a power of two, as large as the CTA
+      // allows for this cell) share a column and test m consecutive entries
+      // of it per round; a ballot gives each accepted entry its position, so
+      // the list is exactly the one a single thread per column would write.
+      {
+        const int nI = ihi - ilo;
+        int m = 1;
+        while (m < 32 && nI * T * (m * 2) <= (int)blockDim.x) m *= 2;
+        const int gpp = T * m;                       // threads per particle
+        const int per_pass = (int)blockDim.x / gpp;  // particles per pass
+        const int r = (int)threadIdx.x & (m - 1);
+        const int g = (int)threadIdx.x / m;
+        const int a_in = g / T, sl = g - (g / T) * T;
+        const int gshift = (int)(threadIdx.x & 31) & ~(m - 1);
+        const unsigned gmask = (m == 32) ? 0xffffffffu : ((1u << m) - 1u);
+        const unsigned below = (1u << r) - 1u;
+        const int rounds = (ncand + gpp - 1) / gpp;
+        for (int i0 = ilo; i0 < ihi; i0 += per_pass) {
+          const int ia = i0 + a_in;
+          const bool act = a_in < per_pass && ia < ihi;
+          const int64_t i = act ? ia : ilo;
           int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
           int k = 0;
           if constexpr (MIX) {
             const uint4 pq_i = p.pq[cur][i];
             const float sc = R.fxs;
             const int tb = (int)pq_i.w * p.ntypes;
-            if (rel) {
-              const float xi = (float)(int)(pq_i.x - ref.x) * sc, yi = (float)(int)(pq_i.y - ref.y) * sc,
-                          zi = (float)(int)(pq_i.z - ref.z) * sc;
-              for (int q = sl; q < ncand; q += T) {
-                const float4 pj = st_f[q];
-                const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + __float_as_int(pj.w)]) {
-                  const int j = st_j[q];
-                  if (j != i) {
-                    if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
-                    ++k;
-                  }
+            // list radii of this particle's row in registers (no dependent
+            // shared-memory load per candidate); entries past ntypes are never selected
+            const float l0 = sh.rl2f[tb], l1 = sh.rl2f[tb + 1], l2 = sh.rl2f[tb + 2], l3 = sh.rl2f[tb + 3];
+            // the particle's own staged position (it is a candidate of its own cell)
+            const int own_q = s_base[nc > 0 ? 13 : 0] + (int)(i - ilo);
+            const float xi = (float)(int)(pq_i.x - ref.x) * sc, yi = (float)(int)(pq_i.y - ref.y) * sc,
+                        zi = (float)(int)(pq_i.z - ref.z) * sc;
+            // SCAN_U rounds at a time: all their shared-memory loads are in
+            // flight together before the tests and the ballots
+            constexpr int SCAN_U = 2;
+            for (int rd0 = 0; rd0 < rounds; rd0 += SCAN_U) {
+              float dx[SCAN_U], dy[SCAN_U], dz[SCAN_U];
+              int wq[SCAN_U];
+              bool ok[SCAN_U];
+#pragma unroll
+              for (int u = 0; u < SCAN_U; ++u) {
+                const int q = sl + T * ((rd0 + u) * m + r);
+                ok[u] = act && q < ncand && q != own_q;
+                const int qq = ok[u] ? q : 0;
+                if (rel) {
+                  const float4 pj = st_f[qq];
+                  dx[u] = xi - pj.x;
+                  dy[u] = yi - pj.y;
+                  dz[u] = zi - pj.z;
+                  wq[u] = __float_as_int(pj.w);
+                } else {
+                  const uint4 pj = st_u[qq];
+                  dx[u] = (float)(int)(pq_i.x - pj.x) * sc;
+                  dy[u] = (float)(int)(pq_i.y - pj.y) * sc;
+                  dz[u] = (float)(int)(pq_i.z - pj.z) * sc;
+                  wq[u] = (int)pj.w;
                 }
               }
-            } else {
-              for (int q = sl; q < ncand; q += T) {
-                const uint4 pj = st_u[q];
-                const float dx = (float)(int)(pq_i.x - pj.x) * sc;
-                const float dy = (float)(int)(pq_i.y - pj.y) * sc;
-                const float dz = (float)(int)(pq_i.z - pj.z) * sc;
-                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rl2f[tb + (int)pj.w]) {
-                  const int j = st_j[q];
-                  if (j != i) {
-                    if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
-                    ++k;
-                  }
+#pragma unroll
+              for (int u = 0; u < SCAN_U; ++u) {
+                const unsigned tj = (unsigned)wq[u] >> 30;
+                const float lim = tj == 0u ? l0 : (tj == 1u ? l1 : (tj == 2u ? l2 : l3));
+                const bool pred = ok[u] && fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u])) < lim;
+                const unsigned bal = (__ballot_sync(0xffffffffu, pred) >> gshift) & gmask;
+                if (pred) {
+                  const int pos = k + __popc(bal & below);
+                  if (pos < p.maxrows) lb[(int64_t)pos * gsz] = wq[u] & 0x3fffffff;
                 }
+                k += __popc(bal);
               }
             }
-            if (sl == 0) p.xbq[i] = pq_i;
+            if (act && r == 0 && sl == 0) p.xbq[i] = pq_i;
           } else {
             const double4_32a pi = p.p4[cur][i];
             const int tb = (int)pi.w * p.ntypes;
             const double L = R.L, hL = 0.5 * R.L;
-            for (int q = sl; q < ncand; q += T) {
-              const double4_32a pj = st_d[q];
-              double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-              if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
-              if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
-              if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
-              const int j = st_j[q];
-              if (j != i && dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
-                if (k < p.maxrows) lb[(int64_t)k * gsz] = j;
-                ++k;
+            for (int rd = 0; rd < rounds; ++rd) {
+              const int q = sl + T * (rd * m + r);
+              bool pred = false;
+              int j = -1;
+              if (act && q < ncand) {
+                const double4_32a pj = st_d[q];
+                double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+                if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+                if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+                if (dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
+                  j = st_j[q];
+                  pred = j != (int)i;
+                }
               }
+              const unsigned bal = (__ballot_sync(0xffffffffu, pred) >> gshift) & gmask;
+              if (pred) {
+                const int pos = k + __popc(bal & below);
+                if (pos < p.maxrows) lb[(int64_t)pos * gsz] = j;
+              }
+              k += __popc(bal);
             }
-            if (sl == 0) p.xbd[i] = pi;
+            if (act && r == 0 && sl == 0) p.xbd[i] = pi;
           }
-          if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
-          p.nnb[i * T + sl] = min(k, p.maxrows);
+          if (act && r == 0) {
+            if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
+            p.nnb[i * T + sl] = min(k, p.maxrows);
+          }
         }
       }
       __syncthreads();
     }
   }
+}
+
+// Cell sort + Verlet list build for every replica whose want_rebuild is set.
+// Returns false after a barrier timeout. *fl receives the last snapshot.
+template <bool MIX>
+__device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t epoch) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nt = p.ntot;
+  // B1: cell index and count per cell; owners copy want -> doing
+  for (int64_t r = gtid; r < p.nrep; r += stride) p.reps[r].doing_rebuild = p.reps[r].want_rebuild;
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.want_rebuild || R.nc == 0) continue;
+    int cx, cy, cz;
+    cell_of_pos<MIX>(p, R, i, cur, cx, cy, cz);
+    const int c = (cz * R.nc + cy) * R.nc + cx;
+    p.cellof[i] = c;
+    atomicAdd(&p.ccount[R.cell0 + c], 1);
+  }
+  int f = grid_sync(p, sh, 101);
+  if (f < 0) return false;
+  // B2: exclusive scan of the cell counts over all packed cells, in chunks of
+  // MD_SCAN_CHUNK cells spread over the grid. B2a: chunk sums, and (last CTA)
+  // each replica's base = particles in the cells of earlier rebuilding replicas.
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAnd(&p.ctl->pending, ~MD_FLAG_REBUILD);
+  const int nchunks = (int)((p.ncells + MD_SCAN_CHUNK - 1) / MD_SCAN_CHUNK);
+  const int cpt = MD_SCAN_CHUNK / (int)blockDim.x;  // cells per thread in a chunk (<= 8)
+  for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
+    const int64_t c0 = (int64_t)k * MD_SCAN_CHUNK;
+    int sum = 0;
+    for (int u = 0; u < cpt; ++u) {
+      const int64_t gc = c0 + u * (int)blockDim.x + threadIdx.x;
+      if (gc < p.ncells) sum += p.ccount[gc];
+    }
+    int total;
+    block_exclusive_scan(sh, sum, &total);
+    if (threadIdx.x == 0) p.chunk[k] = total;
+  }
+  if (blockIdx.x == gridDim.x - 1) {
+    int64_t carry = 0;
+    for (int r0 = 0; r0 < p.nrep; r0 += blockDim.x) {
+      const int r = r0 + (int)threadIdx.x;
+      int v = 0;
+      if (r < p.nrep) {
+        const RepDev& R = p.reps[r];
+        v = (R.doing_rebuild && R.nc > 0) ? R.n : 0;
+      }
+      int total;
+      const int pre = block_exclusive_scan(sh, v, &total);
+      if (r < p.nrep) p.reps[r].cell_base = carry + pre;
+      carry += total;
+    }
+  }
+  f = grid_sync(p, sh, 109);
+  if (f < 0) return false;
+  // B2b: chunk base (sum of the earlier chunks), scan inside the chunk, and
+  // cell start = replica offset + (global prefix - replica base). Cells of
+  // replicas that do not rebuild keep their ranges.
+  for (int64_t r = gtid; r < p.nrep; r += stride) {
+    RepDev& R = p.reps[r];
+    if (!R.doing_rebuild) continue;
+    R.want_rebuild = 0;
+    R.rebuilds += 1;
+    R.rebuild_epoch = epoch;
+    if (R.nc > 0) p.cstart[R.cs0 + R.nc * R.nc * R.nc] = (int)(R.off + R.n);
+  }
+  for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
+    int part = 0;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) part += p.chunk[t];
+    int base;
+    block_exclusive_scan(sh, part, &base);
+    // thread t owns cells c0 + t*cpt .. c0 + t*cpt + cpt - 1 (consecutive)
+    const int64_t c0 = (int64_t)k * MD_SCAN_CHUNK + (int64_t)threadIdx.x * cpt;
+    int v[8], rep[8];
+    int sum = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = u < cpt && c0 + u < p.ncells;
+      v[u] = in ? p.ccount[c0 + u] : 0;
+      rep[u] = in ? p.cell_rep[c0 + u] : -1;
+      sum += v[u];
+    }
+    int total;
+    int run = base + block_exclusive_scan(sh, sum, &total);
+    // replica fields are reloaded only when the replica changes
+    int cur_r = -1;
+    bool r_doing = false;
+    int64_t r_off = 0, r_base = 0, r_cs0 = 0, r_cell0 = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (rep[u] < 0) break;
+      if (rep[u] != cur_r) {
+        const RepDev& R = p.reps[rep[u]];
+        cur_r = rep[u];
+        r_doing = R.doing_rebuild != 0;
+        r_off = R.off;
+        r_base = R.cell_base;
+        r_cs0 = R.cs0;
+        r_cell0 = R.cell0;
+      }
+      const int64_t gc = c0 + u;
+      if (r_doing) {
+        const int start = (int)(r_off + (run - r_base));
+        p.cstart[r_cs0 + (gc - r_cell0)] = start;
+        p.ccursor[gc] = start;
+        p.ccount[gc] = 0;
+      }
+      run += v[u];
+    }
+  }
+  f = grid_sync(p, sh, 102);
+  if (f < 0) return false;
+  // B3: scatter slot indices into their cells (order inside a cell arbitrary)
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
+    const int slot = atomicAdd(&p.ccursor[R.cell0 + p.cellof[i]], 1);
+    p.scat[slot] = (int)i;
+  }
+  f = grid_sync(p, sh, 103);
+  if (f < 0) return false;
+  // B4: rank inside the cell by (type, caller index) (deterministic order) and move
+  // every per-particle array to its new slot in the scratch copy. One warp
+  // per cell: each lane holds one member's caller index and counts, by
+  // shuffles, the members with a smaller one.
+  {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = stride >> 5;
+    for (int64_t gc = gtid >> 5; gc < p.ncells; gc += nwarps) {
+      const RepDev& R = p.reps[p.cell_rep[gc]];
+      if (!R.doing_rebuild || R.nc == 0) continue;
+      const int c = (int)(gc - R.cell0);
+      const int lo = p.cstart[R.cs0 + c], hi = p.cstart[R.cs0 + c + 1];
+      const int n = hi - lo;
+      // key = (type, caller index): particles of one species sit together, so
+      // the lanes of a warp walk lists of similar length
+      for (int e0 = 0; e0 < n; e0 += 32) {
+        int o = -1;
+        unsigned my = 0xffffffffu;
+        if (e0 + lane < n) {
+          o = p.scat[lo + e0 + lane];
+          my = ((unsigned)p.typ[o] << 30) | (unsigned)p.gid[o];
+        }
+        int rank = 0;
+        for (int m0 = 0; m0 < n; m0 += 32) {
+          unsigned other = 0xffffffffu;
+          if (m0 == e0) {
+            other = my;  // the lanes already hold this chunk's keys
+          } else if (m0 + lane < n) {
+            const int oo = p.scat[lo + m0 + lane];
+            other = ((unsigned)p.typ[oo] << 30) | (unsigned)p.gid[oo];
+          }
+          const int lim = min(32, n - m0);
+          for (int t = 0; t < lim; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < my);
+        }
+        if (o < 0) continue;
+        const int64_t d = lo + rank;
+        // every load before any store (the arrays may not be assumed disjoint)
+        const int gd = (int)(my & 0x3fffffffu);
+        const uint8_t ty = (uint8_t)(my >> 30);
+        int im[3];
+        for (int cc = 0; cc < 3; ++cc) im[cc] = p.img[cc * nt + o];
+        if constexpr (MIX) {
+          uint64_t u[3];
+          float v[3], fo[3];
+          for (int cc = 0; cc < 3; ++cc) {
+            u[cc] = p.pfx[cc * nt + o];
+            v[cc] = p.velf[cc * nt + o];
+            fo[cc] = p.frcf[cc * nt + o];
+          }
+          for (int cc = 0; cc < 3; ++cc) {
+            p.t_pfx[cc * nt + d] = u[cc];
+            ((float*)p.t_vel)[cc * nt + d] = v[cc];
+            ((float*)p.t_frc)[cc * nt + d] = fo[cc];
+            p.t_img[cc * nt + d] = im[cc];
+          }
+        } else {
+          const double4_32a x = p.p4[cur][o];
+          double v[3], fo[3];
+          for (int cc = 0; cc < 3; ++cc) {
+            v[cc] = p.veld[cc * nt + o];
+            fo[cc] = p.frcd[cc * nt + o];
+          }
+          p.t_p4[d] = x;
+          for (int cc = 0; cc < 3; ++cc) {
+            ((double*)p.t_vel)[cc * nt + d] = v[cc];
+            ((double*)p.t_frc)[cc * nt + d] = fo[cc];
+            p.t_img[cc * nt + d] = im[cc];
+          }
+        }
+        p.t_gid[d] = gd;
+        p.t_typ[d] = ty;
+      }
+    }
+  }
+  f = grid_sync(p, sh, 104);
+  if (f < 0) return false;
+  // B5: copy back, refresh the gather copy
+  for (int64_t i = gtid; i < nt; i += stride) {
+    const RepDev& R = p.reps[p.tile_rep[i >> 5]];
+    if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
+    const int gd = p.t_gid[i];
+    const uint8_t ty = p.t_typ[i];
+    int im[3];
+    for (int cc = 0; cc < 3; ++cc) im[cc] = p.t_img[cc * nt + i];
+    if constexpr (MIX) {
+      uint64_t u[3];
+      float v[3], fo[3];
+      for (int cc = 0; cc < 3; ++cc) {
+        u[cc] = p.t_pfx[cc * nt + i];
+        v[cc] = ((const float*)p.t_vel)[cc * nt + i];
+        fo[cc] = ((const float*)p.t_frc)[cc * nt + i];
+      }
+      for (int cc = 0; cc < 3; ++cc) {
+        p.pfx[cc * nt + i] = u[cc];
+        p.velf[cc * nt + i] = v[cc];
+        p.frcf[cc * nt + i] = fo[cc];
+        p.img[cc * nt + i] = im[cc];
+      }
+      p.pq[cur][i] = make_uint4((uint32_t)(u[0] >> 32), (uint32_t)(u[1] >> 32), (uint32_t)(u[2] >> 32), ty);
+    } else {
+      const double4_32a x = p.t_p4[i];
+      double v[3], fo[3];
+      for (int cc = 0; cc < 3; ++cc) {
+        v[cc] = ((const double*)p.t_vel)[cc * nt + i];
+        fo[cc] = ((const double*)p.t_frc)[cc * nt + i];
+      }
+      p.p4[cur][i] = x;
+      for (int cc = 0; cc < 3; ++cc) {
+        p.veld[cc * nt + i] = v[cc];
+        p.frcd[cc * nt + i] = fo[cc];
+        p.img[cc * nt + i] = im[cc];
+      }
+    }
+    p.gid[i] = gd;
+    p.typ[i] = ty;
+  }
+  f = grid_sync(p, sh, 105);
+  if (f < 0) return false;
+  // B6: Verlet lists (build_lists)
+  build_lists<MIX>(p, sh, cur);
   f = grid_sync(p, sh, 106);
   if (f < 0) return false;
   *fl = f;
@@ -1122,6 +1337,44 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
 }
 
 // ------------------------------------------------------------------ kernel
+
+// Which SM each CTA runs on (written before the launch's first barrier):
+// CTA rank among the CTAs of its SM, their number, and the SM's index among
+// the SMs in use. Any SM id past the 256-bit map leaves the grid-strided split.
+__device__ void sm_layout(const KParams& p, Shared& sh) {
+  const int mine = p.cta_sm[blockIdx.x];
+  int cnt = 0, rank = 0, bad = 0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
+    const int sj = p.cta_sm[j];
+    if (sj < 0 || sj >= 256) { bad = 1; continue; }
+    atomicOr(&sh.sm_bits[sj >> 5], 1u << (sj & 31));
+    if (sj == mine) {
+      ++cnt;
+      if (j < (int)blockIdx.x) ++rank;
+    }
+  }
+  int tc, tr, tb;
+  block_exclusive_scan(sh, cnt, &tc);
+  block_exclusive_scan(sh, rank, &tr);
+  block_exclusive_scan(sh, bad, &tb);
+  if (threadIdx.x == 0) {
+    int idx = 0, used = 0;
+    if (tb == 0 && mine >= 0 && mine < 256) {
+      for (int w = 0; w < 8; ++w) {
+        const unsigned bits = sh.sm_bits[w];
+        used += __popc(bits);
+        if (w < (mine >> 5)) idx += __popc(bits);
+        else if (w == (mine >> 5)) idx += __popc(bits & ((1u << (mine & 31)) - 1u));
+      }
+    }
+    sh.sm_ok = (tb == 0 && mine >= 0 && mine < 256 && used > 0) ? 1 : 0;
+    sh.sm_idx = idx;
+    sh.sm_used = used;
+    sh.sm_cnt = tc;
+    sh.sm_rank = tr;
+  }
+  __syncthreads();
+}
 
 template <bool MIX>
 __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p) {
@@ -1137,6 +1390,8 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     sh.rl2d[t] = p.rl2_d[t];
     sh.rli2d[t] = p.rli2_d[t];
   }
+  if (threadIdx.x < 8) sh.sm_bits[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) p.cta_sm[blockIdx.x] = sm_id();
   CtlDev* C = p.ctl;
   int cur = C->cur;
   const int drifted = C->drifted;
@@ -1144,6 +1399,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
   const int64_t step0 = C->step;
   int fl = grid_sync(p, sh, 1);
   if (fl < 0) return;
+  sm_layout(p, sh);
   const bool nh = p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT;
   const int kick = p.kind == MD_KIND_NH ? KICK_NH : (p.kind == MD_KIND_NH_EXACT ? KICK_NH_EXACT : KICK_VV);
   int64_t done = 0;
