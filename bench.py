@@ -205,6 +205,38 @@ def run_e2e(torch, kamd, s, dt, steps, T=None):
     return el, h2d, d2h
 
 
+def kernel_sources_digest():
+    """sha256 over the CUDA sources of the library (sorted by name)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2001_07089_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload, tuning):
+    """DRAM bytes (read + write) per launch of the persistent kernel, from the committed ncu summary
+    of this workload, when it was taken on the current kernel sources with the same tuning; else None."""
+    path = os.path.join(ROOT, "profiles", f"md_persistent_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- `") and "`: " in line:
+                k, v = line[3:].split("`: ", 1)
+                fields[k] = v.strip().strip("`")
+    try:
+        same = (fields.get("kernel_sources_sha256") == kernel_sources_digest()
+                and fields.get("tuning") == "{threads_per_atom},{block_size},{skin},{skin_outer}".format(**tuning))
+        return float(fields["dram_bytes_per_launch"]) if same else None
+    except (KeyError, ValueError):
+        return None
+
+
 def cpu_baseline(wl, seconds_target=15.0):
     """The oracle as it stands (one core, all pairs) on a few MD steps of the same system."""
     import oracle
@@ -262,6 +294,8 @@ def main():
     ap.add_argument("--workload", default="ka32k", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed tuning 'threads_per_atom,block_size,skin,skin_outer' instead of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed bench steps of the all-FP64 arm (default: min(steps, 20) for ka32k, 0 otherwise)")
@@ -296,9 +330,12 @@ def main():
 
     # ---- mixed-precision path (the measured value); every rank runs its own system
     s, n_sys, T = setup_system(kamd, wl, "mixed", dev, wk)
+    if args.tuning:
+        t4 = args.tuning.split(",")
+        s.set_tuning(threads_per_atom=int(t4[0]), block_size=int(t4[1]), skin=float(t4[2]), skin_outer=float(t4[3]))
+    elif not args.no_autotune:
+        s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 20)
     tuning = s.tuning
-    if not args.no_autotune:
-        tuning, _ = s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 20)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -364,7 +401,7 @@ def main():
         "fp64": fp64,
         "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload, tuning),
                      "kernel": "md_persistent<mixed> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
         "cpu_baseline": cpu,

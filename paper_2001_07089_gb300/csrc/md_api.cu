@@ -27,7 +27,8 @@ struct md_system {
   int device = 0, nsm = 0;
   int grid = 0;
   int maxrows = 0;
-  int stage_cap = 0;  // candidates the list build stages per cell (dynamic shared memory)
+  int stage_cap = 0;  // candidates the list build stages per group (dynamic shared memory)
+  int gx = 1, gy = 1, gz = 1;  // cells per list-build group
   int64_t ncells = 0;
   bool have_state = false;
   // host mirrors
@@ -65,6 +66,8 @@ struct md_system {
   int32_t* d_ccursor = nullptr;
   int32_t* d_chunk = nullptr;
   int32_t* d_cta_sm = nullptr;  // SM id per CTA of the persistent grid
+  int2* d_grp = nullptr;        // list-build groups (replica, index in replica)
+  int64_t ngroups = 0;
   int cta_sm_cap = 0;
   int32_t* d_scat = nullptr;
   int32_t* d_nbr = nullptr;
@@ -478,17 +481,45 @@ int list_capacity(const md_system* s) {
   return cap;
 }
 
-// Staging area of the list build: the candidates of 27 cells (or of a whole
-// replica too small for cells), with generous headroom over the mean.
-int stage_capacity(const md_system* s) {
+// List-build groups: as many neighbouring cells per CTA (1, 2 or 4 as
+// 1x1x1, 2x1x1, 2x2x1) as keep the CTA's threads busy at T threads per
+// particle. KAMD_LIST_GROUP (1, 2 or 4) overrides the choice.
+void choose_groups(md_system* s) {
+  double occ = 0.0;
+  for (int r = 0; r < s->nrep; ++r) {
+    const RepDev& R = s->reps[r];
+    if (R.nc == 0) continue;
+    const double dens = (double)s->n_per[r] / (R.L * R.L * R.L);
+    occ = std::max(occ, dens * (double)R.cellw * R.cellw * R.cellw);
+  }
+  int g = 1;
+  if (occ > 0.0) {
+    const double fit = (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
+    g = fit >= 4.0 ? 4 : (fit >= 2.0 ? 2 : 1);
+  }
+  if (const char* e = std::getenv("KAMD_LIST_GROUP")) {
+    const int v = std::atoi(e);
+    if (v == 1 || v == 2 || v == 4) g = v;
+  }
+  s->gx = g >= 2 ? 2 : 1;
+  s->gy = g >= 4 ? 2 : 1;
+  s->gz = 1;
+}
+
+// Staging area of the list build: the candidates of the cells around one
+// group, (gx+2)(gy+2)(gz+2) cells (or a whole replica too small for cells),
+// with headroom over the mean (overflow regrows it).
+int stage_capacity(md_system* s) {
+  choose_groups(s);
+  const double nu = (double)(s->gx + 2) * (s->gy + 2) * (s->gz + 2);
   int cap = 64;
   for (int r = 0; r < s->nrep; ++r) {
     const RepDev& R = s->reps[r];
     const double dens = (double)s->n_per[r] / (R.L * R.L * R.L);
     int need;
     if (R.nc > 0) {
-      const double mean = dens * (double)R.cellw * R.cellw * R.cellw;
-      need = (int)std::ceil(27.0 * (1.4 * mean + 12.0));
+      const double mean = nu * dens * (double)R.cellw * R.cellw * R.cellw;
+      need = (int)std::ceil(1.1 * mean + 6.0 * std::sqrt(mean) + 32.0);
     } else {
       need = (int)s->n_per[r];
     }
@@ -516,12 +547,31 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
       const int64_t nc3 = (int64_t)s->reps[r].nc * s->reps[r].nc * s->reps[r].nc;
       for (int64_t c = 0; c < nc3; ++c) cr[s->reps[r].cell0 + c] = r;
     }
-    CK(cudaMemcpy(s->d_cell_rep, cr.data(), 4 * cr.size(), cudaMemcpyHostToDevice));
+    // on the system's stream, after dalloc's clearing memset; cr is a local vector
+    CK(cudaMemcpyAsync(s->d_cell_rep, cr.data(), 4 * cr.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
   }
   CKS(dalloc(s, &s->d_ccount, (size_t)s->ncells));
   CKS(dalloc(s, &s->d_cstart, (size_t)(s->ncells + s->nrep)));
   CKS(dalloc(s, &s->d_ccursor, (size_t)s->ncells));
   CKS(dalloc(s, &s->d_chunk, (size_t)(s->ncells / MD_SCAN_CHUNK + 1)));
+  {
+    std::vector<int2> grp;
+    for (int r = 0; r < s->nrep; ++r) {
+      const int nc = s->reps[r].nc;
+      if (nc == 0) continue;
+      const int ng = ((nc + s->gx - 1) / s->gx) * ((nc + s->gy - 1) / s->gy) * ((nc + s->gz - 1) / s->gz);
+      for (int k = 0; k < ng; ++k) grp.push_back(make_int2(r, k));
+    }
+    s->ngroups = (int64_t)grp.size();
+    dfree(s->d_grp);
+    s->d_grp = nullptr;
+    CKS(dalloc(s, &s->d_grp, std::max<size_t>(grp.size(), 1)));
+    if (!grp.empty()) {
+      CK(cudaMemcpyAsync(s->d_grp, grp.data(), sizeof(int2) * grp.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaStreamSynchronize(s->stream));  // grp is a local vector
+    }
+  }
   const size_t entries = (size_t)s->ntiles * s->maxrows * 32 * T;
   CKS(dalloc(s, &s->d_nbr, entries));
   CKS(dalloc(s, &s->d_nbr_in, entries));
@@ -634,11 +684,16 @@ KParams make_params(const md_system* s) {
   p.cell_rep = s->d_cell_rep;
   p.ncells = s->ncells;
   p.stage_cap = s->stage_cap;
+  p.gx = s->gx;
+  p.gy = s->gy;
+  p.gz = s->gz;
   p.ccount = s->d_ccount;
   p.cstart = s->d_cstart;
   p.ccursor = s->d_ccursor;
   p.chunk = s->d_chunk;
   p.cta_sm = s->d_cta_sm;
+  p.grp = s->d_grp;
+  p.ngroups = s->ngroups;
   p.scat = s->d_scat;
   p.nbr = s->d_nbr;
   p.nnb = s->d_nnb;
@@ -1441,7 +1496,7 @@ void md_destroy(md_system* s) {
   dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
   dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
   dfree(s->d_timg);
-  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_scat);
+  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_grp); dfree(s->d_scat);
   dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
   dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
   dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);

@@ -29,6 +29,8 @@
 #define MD_TILE 32
 #define MD_MAXTYPES 4
 #define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
+#define MD_UNION_MAX 64     // staged cells of one list-build group: (GX+2)(GY+2)(GZ+2) <= 4*4*4
+#define MD_ROWS_MAX 4       // (y, z) rows of cells in one list-build group: GY*GZ <= 4
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
 
 // pending/commit flag bits (grid-uniform decisions)
@@ -108,6 +110,7 @@ struct KParams {
   int ntiles;
   int T;               // lanes per particle
   int maxrows;         // list rows per tile (capacity per particle = maxrows*T)
+  int gx, gy, gz;      // cells per list-build group along x, y, z (1 or 2; gy*gz <= MD_ROWS_MAX)
   int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps
@@ -170,6 +173,8 @@ struct KParams {
   int32_t* ccursor;
   int32_t* chunk;      // per-chunk cell-count sums of the cell scan (MD_SCAN_CHUNK cells each)
   int32_t* cta_sm;     // SM id of each CTA of the current launch
+  const int2* grp;     // list-build groups: (replica, group index inside the replica)
+  int64_t ngroups;
   int32_t* scat;
   int32_t* nbr;        // outer list
   int32_t* nnb;

@@ -840,253 +840,291 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
   return before;
 }
 
+// Scan of one run of staged candidates [qs, qe) for column `sl` of one
+// particle, mixed path. The common test is against the largest list radius
+// of the particle's row (lmax); only the few candidates that pass it are
+// checked against their own pair radius (type in the top bits of w), the
+// particle itself is excluded (own_q) and the entry is stored.
+// REL: staged FP32 coordinates relative to the group's reference particle;
+// otherwise staged fixed-point words and exact integer differences.
+template <bool REL>
+__device__ __forceinline__ int scan_run_mix(const float4* __restrict__ st_f, const uint4* __restrict__ st_u,
+                                            const Shared& sh, int qs, int qe, int T, float x, float y, float z,
+                                            uint4 pq, float sc, int tb, float lmax, int own_q, int32_t* lb,
+                                            int gsz, int maxrows, int k) {
+  for (int q = qs; q < qe; q += T) {
+    float dx, dy, dz;
+    unsigned w;
+    if (REL) {
+      const float4 c = st_f[q];
+      dx = x - c.x;
+      dy = y - c.y;
+      dz = z - c.z;
+      w = (unsigned)__float_as_int(c.w);
+    } else {
+      const uint4 c = st_u[q];
+      dx = (float)(int)(pq.x - c.x) * sc;
+      dy = (float)(int)(pq.y - c.y) * sc;
+      dz = (float)(int)(pq.z - c.z) * sc;
+      w = c.w;
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < lmax) {
+      if (r2 < sh.rl2f[tb + (int)(w >> 30)] && q != own_q) {
+        if (k < maxrows) lb[(int64_t)k * gsz] = (int)(w & 0x3fffffffu);
+        ++k;
+      }
+    }
+  }
+  return k;
+}
+
+// B6: Verlet lists, radius r_c,ab + skin, built per GROUP of up to GX x GY x
+// GZ neighbouring cells (one CTA per group). The union of the cells around
+// the group, (GX+2) x (GY+2) x (GZ+2) cells with x fastest, is staged in
+// shared memory once; each particle of the group then scans the 9 rows of 3
+// staged cells that make up its own 27-cell neighbourhood, list column s
+// taking the entries s, s + T, s + 2T, ... of every row. A replica too small
+// for a 3x3x3 cell grid is one group whose single staged "cell" is the whole
+// replica.
 template <bool MIX>
 __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cur) {
-  // B6: Verlet list over the 27 neighbouring cells (or all particles of a
-  // replica too small for a 3x3x3 cell grid), radius r_c,ab + skin. One CTA
-  // per cell: the candidates of the 27 neighbouring cells are staged in
-  // shared memory (position and slot), then the particles of the cell scan
-  // them, list column s taking every candidate whose index is s mod T, in
-  // candidate order.
-  {
-    const int T = p.T, gsz = 32 * T;
-    extern __shared__ __align__(32) unsigned char dyn[];
-    const int stage_cap = p.stage_cap;
-    double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);            // FP64: positions
-    int32_t* st_j = reinterpret_cast<int32_t*>(dyn + (size_t)stage_cap * (MIX ? 16 : 32));
-    __shared__ int s_lo[27], s_hi[27], s_base[28];
-    const int64_t ncell_all = p.ncells + p.nrep;  // cells, then one pseudo-cell per all-pairs replica
-    int64_t cb, ce, cs;
-    sm_share(sh, ncell_all, 1, 0, &cb, &ce, &cs);
-    for (int64_t gc = cb; gc < ce; gc += cs) {
-      int r;
-      int c = 0;
-      if (gc < p.ncells) r = p.cell_rep[gc];
-      else r = (int)(gc - p.ncells);
-      const RepDev& R = p.reps[r];
-      if (!R.doing_rebuild) continue;
-      if (gc < p.ncells) c = (int)(gc - R.cell0);
-      else if (R.nc != 0) continue;
-      const int nc = R.nc;
-      int ilo, ihi, ncand_cells;
-      if (nc > 0) {
-        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-        if (threadIdx.x < 27) {
-          const int cc = threadIdx.x;
-          const int ox = cc % 3 - 1, oy = (cc / 3) % 3 - 1, oz = cc / 9 - 1;
-          const int q = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
-          s_lo[cc] = p.cstart[R.cs0 + q];
-          s_hi[cc] = p.cstart[R.cs0 + q + 1];
-        }
-        ilo = p.cstart[R.cs0 + c];
-        ihi = p.cstart[R.cs0 + c + 1];
-        ncand_cells = 27;
-      } else {
-        if (threadIdx.x == 0) {
-          s_lo[0] = (int)R.off;
-          s_hi[0] = (int)(R.off + R.n);
-        }
-        ilo = (int)R.off;
-        ihi = (int)(R.off + R.n);
-        ncand_cells = 1;
+  const int T = p.T, gsz = 32 * T;
+  const int GX = p.gx, GY = p.gy, GZ = p.gz;
+  const int UX = GX + 2, UY = GY + 2, UZ = GZ + 2;
+  extern __shared__ __align__(32) unsigned char dyn[];
+  const int stage_cap = p.stage_cap;
+  double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);  // FP64: positions, then slots
+  int32_t* st_j = reinterpret_cast<int32_t*>(dyn + (size_t)stage_cap * 32);
+  float4* st_f = reinterpret_cast<float4*>(dyn);
+  uint4* st_u = reinterpret_cast<uint4*>(dyn);
+  // union cells: first slot, staged base; group rows (ly, lz): first slot,
+  // particle count prefix, slot where the row's second x cell starts
+  __shared__ int s_ulo[MD_UNION_MAX], s_ub[MD_UNION_MAX + 1];
+  __shared__ int s_plo[MD_ROWS_MAX], s_pb[MD_ROWS_MAX + 1], s_px1[MD_ROWS_MAX];
+  __shared__ int s_ref;
+  // groups, then one pseudo-group per all-pairs replica; grid-strided, so
+  // that a rebuild of a few replicas still spreads over every SM
+  const int64_t ngrp_all = p.ngroups + p.nrep;
+  for (int64_t g = blockIdx.x; g < ngrp_all; g += gridDim.x) {
+    int r, lg = 0;
+    if (g < p.ngroups) {
+      const int2 gi = p.grp[g];
+      r = gi.x;
+      lg = gi.y;
+    } else {
+      r = (int)(g - p.ngroups);
+    }
+    const RepDev& R = p.reps[r];
+    if (!R.doing_rebuild) continue;
+    if (g >= p.ngroups && R.nc != 0) continue;
+    const int nc = R.nc;
+    int nu, nrows;
+    if (nc > 0) {
+      const int ngx = (nc + GX - 1) / GX, ngy = (nc + GY - 1) / GY;
+      const int cx = (lg % ngx) * GX, cy = ((lg / ngx) % ngy) * GY, cz = (lg / (ngx * ngy)) * GZ;
+      const int gxe = min(GX, nc - cx), gye = min(GY, nc - cy), gze = min(GZ, nc - cz);
+      nu = UX * UY * UZ;
+      nrows = GY * GZ;
+      for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+        const int ux = t % UX, uy = (t / UX) % UY, uz = t / (UX * UY);
+        const int q = (((cz - 1 + uz + nc) % nc) * nc + (cy - 1 + uy + nc) % nc) * nc + (cx - 1 + ux + nc) % nc;
+        const int lo = p.cstart[R.cs0 + q];
+        s_ulo[t] = lo;
+        s_ub[t] = p.cstart[R.cs0 + q + 1] - lo;  // count for now, prefix below
       }
-      __syncthreads();
-      if (ilo >= ihi) continue;  // empty cell: no particle needs a list
+      for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
+        const int ly = t % GY, lz = t / GY;
+        int lo = 0, n = 0, x1 = 0;
+        if (ly < gye && lz < gze) {
+          const int c0 = ((cz + lz) * nc + (cy + ly)) * nc + cx;  // cells cx .. cx+gxe-1 are consecutive
+          lo = p.cstart[R.cs0 + c0];
+          n = p.cstart[R.cs0 + c0 + gxe] - lo;
+          x1 = gxe > 1 ? p.cstart[R.cs0 + c0 + 1] : lo + n;
+        }
+        s_plo[t] = lo;
+        s_pb[t] = n;
+        s_px1[t] = x1;
+      }
+    } else {
+      nu = 1;
+      nrows = 1;
       if (threadIdx.x == 0) {
-        int b = 0;
-        for (int cc = 0; cc < ncand_cells; ++cc) {
-          s_base[cc] = b;
-          b += s_hi[cc] - s_lo[cc];
+        s_ulo[0] = (int)R.off;
+        s_ub[0] = R.n;
+        s_plo[0] = (int)R.off;
+        s_pb[0] = R.n;
+        s_px1[0] = (int)(R.off + R.n);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // exclusive prefix of the staged-cell counts (nu <= 64: two per lane)
+      const int lane = threadIdx.x;
+      const int c0 = 2 * lane < nu ? s_ub[2 * lane] : 0;
+      const int c1 = 2 * lane + 1 < nu ? s_ub[2 * lane + 1] : 0;
+      int incl = c0 + c1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int excl = incl - c0 - c1;
+      if (2 * lane < nu) s_ub[2 * lane] = excl;
+      if (2 * lane + 1 < nu) s_ub[2 * lane + 1] = excl + c0;
+      if (lane == 31) s_ub[nu] = incl;
+      if (lane == 0) {
+        int m = 0, ref = -1;
+        for (int t = 0; t < nrows; ++t) {
+          const int k = s_pb[t];
+          if (ref < 0 && k > 0) ref = s_plo[t];
+          s_pb[t] = m;
+          m += k;
         }
-        s_base[ncand_cells] = b;
+        s_pb[nrows] = m;
+        s_ref = ref;
       }
+    }
+    __syncthreads();
+    const int ncand = s_ub[nu];
+    const int npart = s_pb[nrows];
+    if (npart == 0) continue;  // empty group: no particle needs a list
+    if (ncand > stage_cap) {
+      // more candidates than the staging area holds: flag and skip (the host regrows it)
+      if (threadIdx.x == 0) raise_flag(p, MD_FLAG_OVERFLOW);
       __syncthreads();
-      const int ncand = s_base[ncand_cells];
-      if (ncand > stage_cap) {
-        // more candidates than the staging area holds: flag and skip (the host regrows it)
-        if (threadIdx.x == 0) raise_flag(p, MD_FLAG_OVERFLOW);
-        __syncthreads();
-        continue;
-      }
-      // mixed path, boxes of >= 5 cells per edge: stage coordinates relative to
-      // the cell's first particle as FP32 (exact integer differences, converted
-      // once per candidate). There every candidate lies within 2 cells of the
-      // reference and the cell's own particles within 1, so differences of
-      // these relative coordinates are the minimum image (their size stays
-      // below L - r_list); the list test has a whole skin of margin, so FP32
-      // is ample. Smaller boxes stage the fixed-point words and test exactly.
-      const bool rel = nc >= 5;
-      uint4 ref = make_uint4(0u, 0u, 0u, 0u);
-      if constexpr (MIX) ref = p.pq[cur][ilo];
-      float4* st_f = reinterpret_cast<float4*>(dyn);
-      uint4* st_u = reinterpret_cast<uint4*>(dyn);
-      // staging, flattened over all candidates: candidate t belongs to the
-      // staged cell cc with s_base[cc] <= t < s_base[cc + 1] (binary search);
-      // each thread issues its STAGE_U loads before any store
-      {
-        constexpr int STAGE_U = 2;
-        const uint4* __restrict__ pqc = p.pq[cur];
-        const double4_32a* __restrict__ p4c = p.p4[cur];
-        for (int t0 = threadIdx.x; t0 < ncand; t0 += STAGE_U * blockDim.x) {
-          int src[STAGE_U];
+      continue;
+    }
+    // mixed path with enough cells per edge: stage coordinates relative to a
+    // particle of the group as FP32 (exact integer differences, converted once
+    // per candidate). Every staged candidate then lies within (G + 1) cells of
+    // the reference along each axis, less than half the box, so differences
+    // of relative coordinates are the minimum image; the list test has a whole
+    // skin of margin, so FP32 is ample. Otherwise the fixed-point words are
+    // staged and every test takes the exact integer difference.
+    const bool rel = MIX && nc >= 2 * GX + 3 && nc >= 2 * GY + 3 && nc >= 2 * GZ + 3;
+    uint4 ref = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (MIX) ref = p.pq[cur][s_ref];
+    {
+      constexpr int STAGE_U = 2;
+      const uint4* __restrict__ pqc = p.pq[cur];
+      const double4_32a* __restrict__ p4c = p.p4[cur];
+      for (int t0 = threadIdx.x; t0 < ncand; t0 += STAGE_U * blockDim.x) {
+        int src[STAGE_U];
+#pragma unroll
+        for (int u = 0; u < STAGE_U; ++u) {
+          const int t = t0 + u * (int)blockDim.x;
+          src[u] = -1;
+          if (t < ncand) {
+            int lo = 0, hi = nu;  // s_ub[lo] <= t < s_ub[hi]
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (s_ub[mid] <= t) lo = mid; else hi = mid;
+            }
+            src[u] = s_ulo[lo] + (t - s_ub[lo]);
+          }
+        }
+        if constexpr (MIX) {
+          uint4 q[STAGE_U];
+#pragma unroll
+          for (int u = 0; u < STAGE_U; ++u)
+            if (src[u] >= 0) q[u] = pqc[src[u]];
+          const float sc = R.fxs;
 #pragma unroll
           for (int u = 0; u < STAGE_U; ++u) {
+            if (src[u] < 0) continue;
             const int t = t0 + u * (int)blockDim.x;
-            src[u] = -1;
-            if (t < ncand) {
-              int lo = 0, hi = ncand_cells;
-              while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_base[mid] <= t) lo = mid; else hi = mid;
-              }
-              src[u] = s_lo[lo] + (t - s_base[lo]);
-            }
+            const unsigned w = (q[u].w << 30) | (unsigned)src[u];
+            if (rel)
+              st_f[t] = make_float4((float)(int)(q[u].x - ref.x) * sc, (float)(int)(q[u].y - ref.y) * sc,
+                                    (float)(int)(q[u].z - ref.z) * sc, __int_as_float((int)w));
+            else
+              st_u[t] = make_uint4(q[u].x, q[u].y, q[u].z, w);
           }
-          if constexpr (MIX) {
-            uint4 q[STAGE_U];
+        } else {
+          double4_32a q[STAGE_U];
 #pragma unroll
-            for (int u = 0; u < STAGE_U; ++u)
-              if (src[u] >= 0) q[u] = pqc[src[u]];
-            const float sc = R.fxs;
+          for (int u = 0; u < STAGE_U; ++u)
+            if (src[u] >= 0) q[u] = p4c[src[u]];
 #pragma unroll
-            for (int u = 0; u < STAGE_U; ++u) {
-              if (src[u] < 0) continue;
-              const int t = t0 + u * (int)blockDim.x;
-              // w = (type << 30) | slot: one 16-byte word per candidate
-              const int w = (int)((q[u].w << 30) | (uint32_t)src[u]);
-              if (rel)
-                st_f[t] = make_float4((float)(int)(q[u].x - ref.x) * sc, (float)(int)(q[u].y - ref.y) * sc,
-                                      (float)(int)(q[u].z - ref.z) * sc, __int_as_float(w));
-              else
-                st_u[t] = make_uint4(q[u].x, q[u].y, q[u].z, (uint32_t)w);
-            }
-          } else {
-            double4_32a q[STAGE_U];
-#pragma unroll
-            for (int u = 0; u < STAGE_U; ++u)
-              if (src[u] >= 0) q[u] = p4c[src[u]];
-#pragma unroll
-            for (int u = 0; u < STAGE_U; ++u) {
-              if (src[u] < 0) continue;
-              const int t = t0 + u * (int)blockDim.x;
-              st_d[t] = q[u];
-              st_j[t] = src[u];
-            }
+          for (int u = 0; u < STAGE_U; ++u) {
+            if (src[u] < 0) continue;
+            const int t = t0 + u * (int)blockDim.x;
+            st_d[t] = q[u];
+            st_j[t] = src[u];
           }
         }
       }
-      __syncthreads();
-      // scan: column s of particle a takes candidates s, s + T, s + 2T, ... in
-      // order. m lanes of one warp (m a power of two, as large as the CTA
-      // allows for this cell) share a column and test m consecutive entries
-      // of it per round; a ballot gives each accepted entry its position, so
-      // the list is exactly the one a single thread per column would write.
-      {
-        const int nI = ihi - ilo;
-        int m = 1;
-        while (m < 32 && nI * T * (m * 2) <= (int)blockDim.x) m *= 2;
-        const int gpp = T * m;                       // threads per particle
-        const int per_pass = (int)blockDim.x / gpp;  // particles per pass
-        const int r = (int)threadIdx.x & (m - 1);
-        const int g = (int)threadIdx.x / m;
-        const int a_in = g / T, sl = g - (g / T) * T;
-        const int gshift = (int)(threadIdx.x & 31) & ~(m - 1);
-        const unsigned gmask = (m == 32) ? 0xffffffffu : ((1u << m) - 1u);
-        const unsigned below = (1u << r) - 1u;
-        const int rounds = (ncand + gpp - 1) / gpp;
-        for (int i0 = ilo; i0 < ihi; i0 += per_pass) {
-          const int ia = i0 + a_in;
-          const bool act = a_in < per_pass && ia < ihi;
-          const int64_t i = act ? ia : ilo;
-          int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
-          int k = 0;
-          if constexpr (MIX) {
-            const uint4 pq_i = p.pq[cur][i];
-            const float sc = R.fxs;
-            const int tb = (int)pq_i.w * p.ntypes;
-            // list radii of this particle's row in registers (no dependent
-            // shared-memory load per candidate); entries past ntypes are never selected
-            const float l0 = sh.rl2f[tb], l1 = sh.rl2f[tb + 1], l2 = sh.rl2f[tb + 2], l3 = sh.rl2f[tb + 3];
-            // the particle's own staged position (it is a candidate of its own cell)
-            const int own_q = s_base[nc > 0 ? 13 : 0] + (int)(i - ilo);
-            const float xi = (float)(int)(pq_i.x - ref.x) * sc, yi = (float)(int)(pq_i.y - ref.y) * sc,
-                        zi = (float)(int)(pq_i.z - ref.z) * sc;
-            // SCAN_U rounds at a time: all their shared-memory loads are in
-            // flight together before the tests and the ballots
-            constexpr int SCAN_U = 2;
-            for (int rd0 = 0; rd0 < rounds; rd0 += SCAN_U) {
-              float dx[SCAN_U], dy[SCAN_U], dz[SCAN_U];
-              int wq[SCAN_U];
-              bool ok[SCAN_U];
-#pragma unroll
-              for (int u = 0; u < SCAN_U; ++u) {
-                const int q = sl + T * ((rd0 + u) * m + r);
-                ok[u] = act && q < ncand && q != own_q;
-                const int qq = ok[u] ? q : 0;
-                if (rel) {
-                  const float4 pj = st_f[qq];
-                  dx[u] = xi - pj.x;
-                  dy[u] = yi - pj.y;
-                  dz[u] = zi - pj.z;
-                  wq[u] = __float_as_int(pj.w);
-                } else {
-                  const uint4 pj = st_u[qq];
-                  dx[u] = (float)(int)(pq_i.x - pj.x) * sc;
-                  dy[u] = (float)(int)(pq_i.y - pj.y) * sc;
-                  dz[u] = (float)(int)(pq_i.z - pj.z) * sc;
-                  wq[u] = (int)pj.w;
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < SCAN_U; ++u) {
-                const unsigned tj = (unsigned)wq[u] >> 30;
-                const float lim = tj == 0u ? l0 : (tj == 1u ? l1 : (tj == 2u ? l2 : l3));
-                const bool pred = ok[u] && fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u])) < lim;
-                const unsigned bal = (__ballot_sync(0xffffffffu, pred) >> gshift) & gmask;
-                if (pred) {
-                  const int pos = k + __popc(bal & below);
-                  if (pos < p.maxrows) lb[(int64_t)pos * gsz] = wq[u] & 0x3fffffff;
-                }
-                k += __popc(bal);
-              }
-            }
-            if (act && r == 0 && sl == 0) p.xbq[i] = pq_i;
-          } else {
-            const double4_32a pi = p.p4[cur][i];
-            const int tb = (int)pi.w * p.ntypes;
-            const double L = R.L, hL = 0.5 * R.L;
-            for (int rd = 0; rd < rounds; ++rd) {
-              const int q = sl + T * (rd * m + r);
-              bool pred = false;
-              int j = -1;
-              if (act && q < ncand) {
-                const double4_32a pj = st_d[q];
-                double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
-                if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
-                if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
-                if (dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
-                  j = st_j[q];
-                  pred = j != (int)i;
-                }
-              }
-              const unsigned bal = (__ballot_sync(0xffffffffu, pred) >> gshift) & gmask;
-              if (pred) {
-                const int pos = k + __popc(bal & below);
-                if (pos < p.maxrows) lb[(int64_t)pos * gsz] = j;
-              }
-              k += __popc(bal);
-            }
-            if (act && r == 0 && sl == 0) p.xbd[i] = pi;
-          }
-          if (act && r == 0) {
-            if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
-            p.nnb[i * T + sl] = min(k, p.maxrows);
-          }
-        }
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    // scan: T threads per particle, particles of the group in row order
+    const int per_pass = (int)blockDim.x / T;
+    const int sl = (int)threadIdx.x % T;
+    for (int pidx = (int)threadIdx.x / T; pidx < npart && (int)threadIdx.x < per_pass * T; pidx += per_pass) {
+      int row = 0;
+      while (pidx >= s_pb[row + 1]) ++row;
+      const int64_t i = s_plo[row] + (pidx - s_pb[row]);
+      const int lx = (nc > 0 && i >= s_px1[row]) ? 1 : 0;
+      const int ly = row % GY, lz = row / GY;
+      // own staged position (each particle is a candidate of its own cell)
+      const int own_u = nc > 0 ? ((lz + 1) * UY + (ly + 1)) * UX + (lx + 1) : 0;
+      const int own_q = s_ub[own_u] + (int)(i - s_ulo[own_u]);
+      int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
+      int k = 0;
+      const int nruns = nc > 0 ? 9 : 1;
+      if constexpr (MIX) {
+        const uint4 pq_i = p.pq[cur][i];
+        const float sc = R.fxs;
+        const float x = (float)(int)(pq_i.x - ref.x) * sc;
+        const float y = (float)(int)(pq_i.y - ref.y) * sc;
+        const float z = (float)(int)(pq_i.z - ref.z) * sc;
+        const int tb = (int)pq_i.w * p.ntypes;
+        float lmax = 0.0f;
+        for (int t = 0; t < p.ntypes; ++t) lmax = fmaxf(lmax, sh.rl2f[tb + t]);
+        for (int run = 0; run < nruns; ++run) {
+          int qs = 0, qe = ncand;
+          if (nc > 0) {
+            const int us0 = ((lz + run / 3) * UY + (ly + run % 3)) * UX + lx;
+            qs = s_ub[us0];
+            qe = s_ub[us0 + 3];
+          }
+          if (rel)
+            k = scan_run_mix<true>(st_f, st_u, sh, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
+                                   p.maxrows, k);
+          else
+            k = scan_run_mix<false>(st_f, st_u, sh, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
+                                    p.maxrows, k);
+        }
+        if (sl == 0) p.xbq[i] = pq_i;
+      } else {
+        const double4_32a pi = p.p4[cur][i];
+        const int tb = (int)pi.w * p.ntypes;
+        const double L = R.L, hL = 0.5 * R.L;
+        for (int run = 0; run < nruns; ++run) {
+          int qs = 0, qe = ncand;
+          if (nc > 0) {
+            const int us0 = ((lz + run / 3) * UY + (ly + run % 3)) * UX + lx;
+            qs = s_ub[us0];
+            qe = s_ub[us0 + 3];
+          }
+          for (int q = qs + sl; q < qe; q += T) {
+            const double4_32a pj = st_d[q];
+            double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
+            if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
+            if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
+            if (q != own_q && dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
+              if (k < p.maxrows) lb[(int64_t)k * gsz] = st_j[q];
+              ++k;
+            }
+          }
+        }
+        if (sl == 0) p.xbd[i] = pi;
+      }
+      if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
+      p.nnb[i * T + sl] = min(k, p.maxrows);
+    }
+    __syncthreads();
   }
 }
 
