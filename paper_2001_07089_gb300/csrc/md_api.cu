@@ -385,10 +385,10 @@ __global__ void k_count_pairs(bool mixed, int64_t ntot, int T, int maxrows, int 
   const int gsz = 32 * T;
   unsigned long long c = 0;
   for (int s = 0; s < T; ++s) {
-    const int32_t* lb = nbr + (i >> 5) * (int64_t)maxrows * gsz + (i & 31) * T + s;
+    const int32_t* lb = nbr + list_col(i >> 5, maxrows, T, (int)(i & 31) * T + s);
     const int cnt = nnb[i * T + s];
     for (int q = 0; q < cnt; ++q) {
-      const int j = lb[(int64_t)q * gsz];
+      const int j = lb[list_at(0, q, gsz)];
       if (mixed) {
         const uint4 a = pq[i], b = pq[j];
         const float dx = (float)(int)(a.x - b.x) * R.fxs, dy = (float)(int)(a.y - b.y) * R.fxs,
@@ -539,7 +539,7 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   dfree(s->d_nbr);
   dfree(s->d_nbr_in);
   dfree(s->d_cell_rep);
-  s->maxrows = (cap_entries + T - 1) / T;
+  s->maxrows = ((cap_entries + T - 1) / T + 3) / 4 * 4;  // list layout: whole quads per column
   CKS(dalloc(s, &s->d_cell_rep, (size_t)s->ncells));
   {
     std::vector<int32_t> cr((size_t)std::max<int64_t>(s->ncells, 1), 0);

@@ -102,6 +102,19 @@ struct ThermoDev {  // layout identical to md_thermo
   double T, pe_per_n, ke_per_n, etot_per_n, virial, h_nh, xi;
 };
 
+// Verlet list layout. A tile of 32 particles owns maxrows * 32T entries
+// (maxrows a multiple of 4). List column L = a*T + s belongs to lane s of the
+// tile's particle a. Entries are grouped in quads: entry q of column L sits at
+//   tile * maxrows * 32T  +  (q / 4) * 4 * 32T  +  4 L  +  q % 4,
+// so the 32 lanes of a warp that read one quad each touch 512 contiguous
+// bytes, and a writer stores four entries with one 16-byte store.
+__host__ __device__ inline int64_t list_col(int64_t tile, int maxrows, int T, int col) {
+  return tile * (int64_t)maxrows * 32 * T + 4 * (int64_t)col;
+}
+__host__ __device__ inline int64_t list_at(int64_t colbase, int q, int gsz) {
+  return colbase + (int64_t)(q >> 2) * 4 * gsz + (q & 3);
+}
+
 struct KParams {
   // sizes
   int nrep;
@@ -109,7 +122,7 @@ struct KParams {
   int64_t ntot;        // slots
   int ntiles;
   int T;               // lanes per particle
-  int maxrows;         // list rows per tile (capacity per particle = maxrows*T)
+  int maxrows;         // list entries per column (capacity per particle = maxrows*T), a multiple of 4
   int gx, gy, gz;      // cells per list-build group along x, y, z (1 or 2; gy*gz <= MD_ROWS_MAX)
   int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b

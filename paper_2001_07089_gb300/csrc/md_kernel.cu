@@ -356,27 +356,30 @@ __device__ __forceinline__ void pair_mix(const Shared& sh, const uint4& pi, cons
   }
 }
 
-// Walk one lane's column of the list: indices are loaded one batch of 4
-// ahead of the gathers they feed, so list and position latencies overlap.
+// Walk one lane's column of the list: each quad of indices is one 16-byte
+// load, issued one quad ahead of the gathers it feeds, so list and position
+// latencies overlap.
 template <bool ENERGY>
 __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __restrict__ pq, const int* lp, int gsz,
                                              int cnt, const uint4& pi, int tb, float sc, float& fx, float& fy,
                                              float& fz, float& pe, float& vir) {
+  const int64_t qstride = 4 * (int64_t)gsz;  // ints between consecutive quads of one column
+  int4 jq = make_int4(0, 0, 0, 0);
+  if (cnt > 0) jq = *reinterpret_cast<const int4*>(lp);
   int q = 0;
-  int j0 = 0, j1 = 0, j2 = 0, j3 = 0;
-  if (cnt >= 4) { j0 = lp[0]; j1 = lp[gsz]; j2 = lp[2 * gsz]; j3 = lp[3 * gsz]; }
   for (; q + 4 <= cnt; q += 4) {
-    const uint4 p0 = pq[j0], p1 = pq[j1], p2 = pq[j2], p3 = pq[j3];
-    if (q + 8 <= cnt) {
-      const int* nx = lp + (int64_t)(q + 4) * gsz;
-      j0 = nx[0]; j1 = nx[gsz]; j2 = nx[2 * gsz]; j3 = nx[3 * gsz];
-    }
+    const uint4 p0 = pq[jq.x], p1 = pq[jq.y], p2 = pq[jq.z], p3 = pq[jq.w];
+    if (q + 4 < cnt) jq = *reinterpret_cast<const int4*>(lp + (int64_t)((q + 4) >> 2) * qstride);
     pair_mix<ENERGY>(sh, pi, p0, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p1, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p2, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p3, tb, sc, fx, fy, fz, pe, vir);
   }
-  for (; q < cnt; ++q) pair_mix<ENERGY>(sh, pi, pq[lp[(int64_t)q * gsz]], tb, sc, fx, fy, fz, pe, vir);
+  // tail: 1 to 3 entries of the last quad, already in jq
+  const int r = cnt - q;
+  if (r > 0) pair_mix<ENERGY>(sh, pi, pq[jq.x], tb, sc, fx, fy, fz, pe, vir);
+  if (r > 1) pair_mix<ENERGY>(sh, pi, pq[jq.y], tb, sc, fx, fy, fz, pe, vir);
+  if (r > 2) pair_mix<ENERGY>(sh, pi, pq[jq.z], tb, sc, fx, fy, fz, pe, vir);
 }
 
 // Force phase. The work unit is one warp: 32/T particles of one tile with T
@@ -404,7 +407,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
     const int rr = w * 32 + lane;
     const int a = rr / T, s = rr - a * T;
     const int64_t i = (int64_t)tile * 32 + a;
-    const int* lp = p.nbr_in + (int64_t)tile * p.maxrows * gsz + a * T + s;
+    const int* lp = p.nbr_in + list_col(tile, p.maxrows, T, a * T + s);
     if constexpr (MIX) {
       // the particle's own data does not depend on its replica: issue these
       // loads first so that they overlap the replica lookup
@@ -482,7 +485,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         const int tb = (int)pi.w * p.ntypes;
         const double L = R->L, hL = 0.5 * R->L;
         for (int q = 0; q < cnt; ++q) {
-          const int j = lp[(int64_t)q * gsz];
+          const int j = lp[list_at(0, q, gsz)];
           const double4_32a pj = p4[j];
           double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
@@ -578,7 +581,7 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
     if ((tile - R.tile0) * 32 + a >= R.n) continue;
     // only replicas with a particle past half the inner skin, or a new outer list
     if (R.prune_epoch != epoch && R.rebuild_epoch != epoch) continue;
-    const int64_t off = (int64_t)tile * p.maxrows * gsz + a * T + s;
+    const int64_t off = list_col(tile, p.maxrows, T, a * T + s);
     const int* lo = p.nbr + off;
     int* li = p.nbr_in + off;
     const int cnt = p.nnb[i * T + s];
@@ -589,13 +592,13 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
       const int tb = (int)pi.w * p.ntypes;
       const float sc = R.fxs;
       for (int q = 0; q < cnt; ++q) {
-        const int j = lo[(int64_t)q * gsz];
+        const int j = lo[list_at(0, q, gsz)];
         const uint4 pj = pq[j];
         const float dx = (float)(int)(pi.x - pj.x) * sc;
         const float dy = (float)(int)(pi.y - pj.y) * sc;
         const float dz = (float)(int)(pi.z - pj.z) * sc;
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj.w]) {
-          li[(int64_t)k * gsz] = j;
+          li[list_at(0, k, gsz)] = j;
           ++k;
         }
       }
@@ -606,14 +609,14 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
       const int tb = (int)pi.w * p.ntypes;
       const double L = R.L, hL = 0.5 * R.L;
       for (int q = 0; q < cnt; ++q) {
-        const int j = lo[(int64_t)q * gsz];
+        const int j = lo[list_at(0, q, gsz)];
         const double4_32a pj = p4[j];
         double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
         if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
         if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
         if (dx * dx + dy * dy + dz * dz < sh.rli2d[tb + (int)pj.w]) {
-          li[(int64_t)k * gsz] = j;
+          li[list_at(0, k, gsz)] = j;
           ++k;
         }
       }
@@ -847,33 +850,50 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
 // particle itself is excluded (own_q) and the entry is stored.
 // REL: staged FP32 coordinates relative to the group's reference particle;
 // otherwise staged fixed-point words and exact integer differences.
+// Accepted entries pass through a 4-deep shift register (b1, b2, b3 plus the
+// new one); every fourth entry completes a quad, stored with one 16-byte store.
+__device__ __forceinline__ void list_push(int32_t* col, int gsz, int maxrows, int& k, int& b1, int& b2, int& b3,
+                                          int j) {
+  if ((k & 3) == 3 && k < maxrows)
+    *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = make_int4(b1, b2, b3, j);
+  b1 = b2;
+  b2 = b3;
+  b3 = j;
+  ++k;
+}
+
+// Store the last, partial quad of a column (k % 4 entries in b1..b3).
+__device__ __forceinline__ void list_flush(int32_t* col, int gsz, int maxrows, int k, int b1, int b2, int b3) {
+  const int r = k & 3;
+  if (r == 0 || k - r >= maxrows) return;
+  const int4 v = r == 1 ? make_int4(b3, 0, 0, 0) : (r == 2 ? make_int4(b2, b3, 0, 0) : make_int4(b1, b2, b3, 0));
+  *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = v;
+}
+
 template <bool REL>
-__device__ __forceinline__ int scan_run_mix(const float4* __restrict__ st_f, const uint4* __restrict__ st_u,
-                                            const Shared& sh, int qs, int qe, int T, float x, float y, float z,
-                                            uint4 pq, float sc, int tb, float lmax, int own_q, int32_t* lb,
-                                            int gsz, int maxrows, int k) {
+__device__ __forceinline__ int scan_run_mix(uint32_t st_s, uint32_t rl2_s, int qs, int qe, int T, float x, float y,
+                                            float z, uint4 pq, float sc, int tb, float lmax, int own_q, int32_t* col,
+                                            int gsz, int maxrows, int k, int& b1, int& b2, int& b3) {
+  // st_s, rl2_s: shared-window addresses of the staged candidates (16 bytes
+  // each) and of the list-radius table, read with explicit shared loads
   for (int q = qs; q < qe; q += T) {
+    uint32_t c0, c1, c2, c3;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3) : "r"(st_s + 16u * (uint32_t)q));
     float dx, dy, dz;
-    unsigned w;
     if (REL) {
-      const float4 c = st_f[q];
-      dx = x - c.x;
-      dy = y - c.y;
-      dz = z - c.z;
-      w = (unsigned)__float_as_int(c.w);
+      dx = x - __uint_as_float(c0);
+      dy = y - __uint_as_float(c1);
+      dz = z - __uint_as_float(c2);
     } else {
-      const uint4 c = st_u[q];
-      dx = (float)(int)(pq.x - c.x) * sc;
-      dy = (float)(int)(pq.y - c.y) * sc;
-      dz = (float)(int)(pq.z - c.z) * sc;
-      w = c.w;
+      dx = (float)(int)(pq.x - c0) * sc;
+      dy = (float)(int)(pq.y - c1) * sc;
+      dz = (float)(int)(pq.z - c2) * sc;
     }
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 < lmax) {
-      if (r2 < sh.rl2f[tb + (int)(w >> 30)] && q != own_q) {
-        if (k < maxrows) lb[(int64_t)k * gsz] = (int)(w & 0x3fffffffu);
-        ++k;
-      }
+      float lim;
+      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(lim) : "r"(rl2_s + 4u * (uint32_t)(tb + (int)(c3 >> 30))));
+      if (r2 < lim && q != own_q) list_push(col, gsz, maxrows, k, b1, b2, b3, (int)(c3 & 0x3fffffffu));
     }
   }
   return k;
@@ -1069,8 +1089,9 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
       // own staged position (each particle is a candidate of its own cell)
       const int own_u = nc > 0 ? ((lz + 1) * UY + (ly + 1)) * UX + (lx + 1) : 0;
       const int own_q = s_ub[own_u] + (int)(i - s_ulo[own_u]);
-      int32_t* lb = p.nbr + (i >> 5) * (int64_t)p.maxrows * gsz + (i & 31) * T + sl;
+      int32_t* lb = p.nbr + list_col(i >> 5, p.maxrows, T, (int)(i & 31) * T + sl);
       int k = 0;
+      int b1 = 0, b2 = 0, b3 = 0;  // quad shift register of the list writer
       const int nruns = nc > 0 ? 9 : 1;
       if constexpr (MIX) {
         const uint4 pq_i = p.pq[cur][i];
@@ -1081,19 +1102,38 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         const int tb = (int)pq_i.w * p.ntypes;
         float lmax = 0.0f;
         for (int t = 0; t < p.ntypes; ++t) lmax = fmaxf(lmax, sh.rl2f[tb + t]);
+        const uint32_t st_s = (uint32_t)__cvta_generic_to_shared(dyn);
+        const uint32_t rl2_s = (uint32_t)__cvta_generic_to_shared(sh.rl2f);
+        const int maxrows = p.maxrows;
+        // position inside the own cell (the binning of B1: cell = (u * nc) >> 32,
+        // so the low word of u * nc is the fraction), for culling the
+        // neighbour cells that lie wholly beyond the largest list radius of
+        // this particle's row. A cell is at least r_list wide, so only the
+        // images at offsets -1, 0, +1 can come within reach.
+        const float wc = R.cellw;
+        const float f2w = wc * 2.3283064365386963e-10f;  // cell width / 2^32
+        const float fxl = (float)(uint32_t)((uint64_t)pq_i.x * (uint64_t)nc) * f2w;
+        const float fyl = (float)(uint32_t)((uint64_t)pq_i.y * (uint64_t)nc) * f2w;
+        const float fzl = (float)(uint32_t)((uint64_t)pq_i.z * (uint64_t)nc) * f2w;
+        const float lcut = (sqrtf(lmax) + 1e-3f * wc) * (sqrtf(lmax) + 1e-3f * wc);  // rounding margin
         for (int run = 0; run < nruns; ++run) {
           int qs = 0, qe = ncand;
           if (nc > 0) {
+            const int oy = run % 3 - 1, oz = run / 3 - 1;
+            const float ey = oy < 0 ? fyl : (oy > 0 ? wc - fyl : 0.0f);
+            const float ez = oz < 0 ? fzl : (oz > 0 ? wc - fzl : 0.0f);
+            const float d2 = fmaf(ey, ey, ez * ez);
+            if (d2 >= lcut) continue;  // the whole row is out of reach
             const int us0 = ((lz + run / 3) * UY + (ly + run % 3)) * UX + lx;
-            qs = s_ub[us0];
-            qe = s_ub[us0 + 3];
+            qs = s_ub[us0 + (fmaf(fxl, fxl, d2) < lcut ? 0 : 1)];
+            qe = s_ub[us0 + (fmaf(wc - fxl, wc - fxl, d2) < lcut ? 3 : 2)];
           }
           if (rel)
-            k = scan_run_mix<true>(st_f, st_u, sh, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
-                                   p.maxrows, k);
+            k = scan_run_mix<true>(st_s, rl2_s, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz, maxrows,
+                                   k, b1, b2, b3);
           else
-            k = scan_run_mix<false>(st_f, st_u, sh, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
-                                    p.maxrows, k);
+            k = scan_run_mix<false>(st_s, rl2_s, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
+                                    maxrows, k, b1, b2, b3);
         }
         if (sl == 0) p.xbq[i] = pq_i;
       } else {
@@ -1114,13 +1154,13 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
             if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
             if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
             if (q != own_q && dx * dx + dy * dy + dz * dz < sh.rl2d[tb + (int)pj.w]) {
-              if (k < p.maxrows) lb[(int64_t)k * gsz] = st_j[q];
-              ++k;
+              list_push(lb, gsz, p.maxrows, k, b1, b2, b3, st_j[q]);
             }
           }
         }
         if (sl == 0) p.xbd[i] = pi;
       }
+      list_flush(lb, gsz, p.maxrows, k, b1, b2, b3);
       if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
       p.nnb[i * T + sl] = min(k, p.maxrows);
     }
