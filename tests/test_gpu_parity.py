@@ -88,6 +88,30 @@ def test_forces_32k_tiled_melt(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("group", ["1", "2", "4"])
+@pytest.mark.parametrize("n,tile", [(1000, 1), (4000, 1), (4000, 2)], ids=["1000", "4000", "32000-tiled"])
+def test_list_build_every_group_shape(prec, group, n, tile, monkeypatch):
+    """The list build works on groups of 1, 2 or 4 cells (1x1x1, 2x1x1, 2x2x1). Every shape, on boxes
+    of 3 cells per edge (exact fixed-point test), 5 (FP32 relative coordinates for single cells,
+    exact for groups) and 10 (relative coordinates for every shape), gives the oracle's forces with
+    every lane split."""
+    pos, vel, types, L = melted(n, 23 if n == 4000 else 22, nsteps=200)
+    if tile > 1:
+        shifts = np.array([[i, j, k] for i in range(tile) for j in range(tile) for k in range(tile)], dtype=float) * L
+        pos = np.concatenate([pos + sh for sh in shifts])
+        vel = np.concatenate([vel] * tile ** 3)
+        types = np.concatenate([types] * tile ** 3)
+        L = tile * L
+    f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
+    monkeypatch.setenv("KAMD_LIST_GROUP", group)
+    for tpa in (1, 4):
+        with make_system(len(pos), L, types, prec, tpa=tpa) as s:
+            s.set_state(pos, vel)
+            f, pe, _ = s.forces()
+        check_forces(f, f_ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_forces_32k_lattice_start(prec):
     """The 32k configuration's own start: 32^3 lattice sites (32 000 occupied), jitter 0.05."""
     n = 32000
