@@ -870,30 +870,56 @@ __device__ __forceinline__ void list_flush(int32_t* col, int gsz, int maxrows, i
   *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = v;
 }
 
+// Distance^2 of staged candidate q from the particle (mixed path); *w gets
+// the candidate's (type << 30) | slot word.
+template <bool REL>
+__device__ __forceinline__ float cand_r2(uint32_t st_s, int q, float x, float y, float z, const uint4& pq, float sc,
+                                         uint32_t* w) {
+  uint32_t c0, c1, c2, c3;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3) : "r"(st_s + 16u * (uint32_t)q));
+  float dx, dy, dz;
+  if (REL) {
+    dx = x - __uint_as_float(c0);
+    dy = y - __uint_as_float(c1);
+    dz = z - __uint_as_float(c2);
+  } else {
+    dx = (float)(int)(pq.x - c0) * sc;
+    dy = (float)(int)(pq.y - c1) * sc;
+    dz = (float)(int)(pq.z - c2) * sc;
+  }
+  *w = c3;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 template <bool REL>
 __device__ __forceinline__ int scan_run_mix(uint32_t st_s, uint32_t rl2_s, int qs, int qe, int T, float x, float y,
                                             float z, uint4 pq, float sc, int tb, float lmax, int own_q, int32_t* col,
                                             int gsz, int maxrows, int k, int& b1, int& b2, int& b3) {
   // st_s, rl2_s: shared-window addresses of the staged candidates (16 bytes
-  // each) and of the list-radius table, read with explicit shared loads
-  for (int q = qs; q < qe; q += T) {
-    uint32_t c0, c1, c2, c3;
-    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3) : "r"(st_s + 16u * (uint32_t)q));
-    float dx, dy, dz;
-    if (REL) {
-      dx = x - __uint_as_float(c0);
-      dy = y - __uint_as_float(c1);
-      dz = z - __uint_as_float(c2);
-    } else {
-      dx = (float)(int)(pq.x - c0) * sc;
-      dy = (float)(int)(pq.y - c1) * sc;
-      dz = (float)(int)(pq.z - c2) * sc;
+  // each) and of the list-radius table. Chunks of up to 32 of this column's
+  // candidates: a first, branch-free pass marks those within the largest list
+  // radius of the row (lmax) in a bit mask; a second pass visits only the
+  // marked ones, in candidate order, checks their pair radius and the
+  // self-exclusion and stores them. The costly accept path then runs once
+  // per near candidate instead of once per candidate for the whole warp.
+  for (int q0 = qs; q0 < qe; q0 += 32 * T) {
+    const int nq = min(32, (qe - q0 + T - 1) / T);
+    unsigned mask = 0u;
+#pragma unroll 4
+    for (int u = 0; u < nq; ++u) {
+      uint32_t w;
+      const float r2 = cand_r2<REL>(st_s, q0 + u * T, x, y, z, pq, sc, &w);
+      mask |= (r2 < lmax ? 1u : 0u) << u;
     }
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 < lmax) {
+    while (mask) {
+      const int u = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int q = q0 + u * T;
+      uint32_t w;
+      const float r2 = cand_r2<REL>(st_s, q, x, y, z, pq, sc, &w);
       float lim;
-      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(lim) : "r"(rl2_s + 4u * (uint32_t)(tb + (int)(c3 >> 30))));
-      if (r2 < lim && q != own_q) list_push(col, gsz, maxrows, k, b1, b2, b3, (int)(c3 & 0x3fffffffu));
+      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(lim) : "r"(rl2_s + 4u * (uint32_t)(tb + (int)(w >> 30))));
+      if (r2 < lim && q != own_q) list_push(col, gsz, maxrows, k, b1, b2, b3, (int)(w & 0x3fffffffu));
     }
   }
   return k;
