@@ -67,6 +67,12 @@ struct md_system {
   int32_t* d_chunk = nullptr;
   int32_t* d_cta_sm = nullptr;  // SM id per CTA of the persistent grid
   int2* d_grp = nullptr;        // list-build groups (replica, index in replica)
+  int2* d_redmap = nullptr;     // reduction chunks (replica, chunk index)
+  int2* d_redrep = nullptr;     // per replica (first chunk, chunks)
+  double* d_redpart = nullptr;  // chunk sums
+  int64_t nred = 0;
+  int red2 = 0;
+  int red_tiles = MD_RED_TILES;
   int64_t ngroups = 0;
   int cta_sm_cap = 0;
   int32_t* d_scat = nullptr;
@@ -566,6 +572,37 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
       for (int k = 0; k < ng; ++k) grp.push_back(make_int2(r, k));
     }
     s->ngroups = (int64_t)grp.size();
+    // two-level reductions once a replica spans more than red_tiles tiles
+    // (KAMD_RED_TILES overrides the chunk size, for tests of that path)
+    s->red_tiles = MD_RED_TILES;
+    if (const char* e = std::getenv("KAMD_RED_TILES")) {
+      const int v = std::atoi(e);
+      if (v >= 1) s->red_tiles = v;
+    }
+    std::vector<int2> rmap, rrep;
+    int maxch = 1;
+    for (int r = 0; r < s->nrep; ++r) {
+      const int nch = (s->reps[r].ntiles + s->red_tiles - 1) / s->red_tiles;
+      rrep.push_back(make_int2((int)rmap.size(), nch));
+      for (int c = 0; c < nch; ++c) rmap.push_back(make_int2(r, c));
+      maxch = std::max(maxch, nch);
+    }
+    s->red2 = maxch > 1 ? 1 : 0;
+    s->nred = (int64_t)rmap.size();
+    dfree(s->d_redmap);
+    dfree(s->d_redrep);
+    dfree(s->d_redpart);
+    s->d_redmap = nullptr;
+    s->d_redrep = nullptr;
+    s->d_redpart = nullptr;
+    CKS(dalloc(s, &s->d_redmap, std::max<size_t>(rmap.size(), 1)));
+    CKS(dalloc(s, &s->d_redrep, std::max<size_t>(rrep.size(), 1)));
+    CKS(dalloc(s, &s->d_redpart, std::max<size_t>(rmap.size(), 1) * MD_NPART));
+    if (!rmap.empty()) {
+      CK(cudaMemcpyAsync(s->d_redmap, rmap.data(), sizeof(int2) * rmap.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaMemcpyAsync(s->d_redrep, rrep.data(), sizeof(int2) * rrep.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaStreamSynchronize(s->stream));  // local vectors
+    }
     dfree(s->d_grp);
     s->d_grp = nullptr;
     CKS(dalloc(s, &s->d_grp, std::max<size_t>(grp.size(), 1)));
@@ -696,6 +733,12 @@ KParams make_params(const md_system* s) {
   p.cta_sm = s->d_cta_sm;
   p.grp = s->d_grp;
   p.ngroups = s->ngroups;
+  p.red2 = s->red2;
+  p.red_tiles = s->red_tiles;
+  p.nred = s->nred;
+  p.redmap = s->d_redmap;
+  p.redrep = s->d_redrep;
+  p.redpart = s->d_redpart;
   p.scat = s->d_scat;
   p.nbr = s->d_nbr;
   p.nnb = s->d_nnb;
@@ -1498,7 +1541,7 @@ void md_destroy(md_system* s) {
   dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
   dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
   dfree(s->d_timg);
-  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_grp); dfree(s->d_scat);
+  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_grp); dfree(s->d_redmap); dfree(s->d_redrep); dfree(s->d_redpart); dfree(s->d_scat);
   dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
   dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
   dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);

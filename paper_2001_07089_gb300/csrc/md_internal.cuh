@@ -31,6 +31,7 @@
 #define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
 #define MD_UNION_MAX 64     // staged cells of one list-build group: (GX+2)(GY+2)(GZ+2) <= 4*4*4
 #define MD_ROWS_MAX 4       // (y, z) rows of cells in one list-build group: GY*GZ <= 4
+#define MD_RED_TILES 1024   // tiles per chunk of the two-level per-replica reduction (default)
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
 
 // pending/commit flag bits (grid-uniform decisions)
@@ -187,6 +188,12 @@ struct KParams {
   int32_t* chunk;      // per-chunk cell-count sums of the cell scan (MD_SCAN_CHUNK cells each)
   int32_t* cta_sm;     // SM id of each CTA of the current launch
   const int2* grp;     // list-build groups: (replica, group index inside the replica)
+  int red2;            // 1: reductions in two levels (some replica has more than red_tiles tiles)
+  int red_tiles;       // tiles per reduction chunk
+  int64_t nred;        // reduction chunks over all replicas
+  const int2* redmap;  // chunk -> (replica, chunk index inside the replica)
+  const int2* redrep;  // replica -> (first chunk, number of chunks)
+  double* redpart;     // chunk sums, MD_NPART doubles per chunk
   int64_t ngroups;
   int32_t* scat;
   int32_t* nbr;        // outer list

@@ -686,70 +686,109 @@ __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* par
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh);
 
-// One CTA per replica: the replica's partial units (upt per tile) are summed
-// thread-strided in fixed order (float-float for the mixed path, double for
-// FP64), then warp trees and the CTA's warps in order; thread 0 applies the
-// scalar updates of the mode and, if asked, writes one thermo record.
+// Sum of the partial records [u0, u0 + nu) (fixed order): thread-strided
+// float-float (mixed) or double accumulation, warp trees, then the CTA's
+// warps in order. Thread 0 receives the six totals in acc.
 template <bool MIX>
-__device__ void reduce_phase(const KParams& p, Shared& sh, const double* part, int upt, int mode, int64_t step,
-                             bool log_now, int64_t log_idx) {
+__device__ void sum_records(Shared& sh, const double* part, int64_t u0, int64_t nu, double* acc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const bool nh = (p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT) && p.op == MD_OP_STEPS;
-  for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
-    RepDev& R = p.reps[r];
-    const int64_t u0 = (int64_t)R.tile0 * upt, nu = (int64_t)R.ntiles * upt;
-    double acc[6];
-    if constexpr (MIX) {
-      ff a[6];
+  if constexpr (MIX) {
+    ff a[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) a[k] = ff{0.f, 0.f};
-      const float2* q0 = reinterpret_cast<const float2*>(part);
-      for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
-        const float2* q = q0 + (u0 + t) * MD_NPART;
+    for (int k = 0; k < 6; ++k) a[k] = ff{0.f, 0.f};
+    const float2* q0 = reinterpret_cast<const float2*>(part);
+    for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+      const float2* q = q0 + (u0 + t) * MD_NPART;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] = ff_add(a[k], ff{q[k].x, q[k].y});
-      }
-      float2* red = reinterpret_cast<float2*>(&sh.red[0][0]);
+      for (int k = 0; k < 6; ++k) a[k] = ff_add(a[k], ff{q[k].x, q[k].y});
+    }
+    float2* red = reinterpret_cast<float2*>(&sh.red[0][0]);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        a[k] = warp_sum_ff(a[k]);
-        if (lane == 0) red[warp * MD_NPART + k] = make_float2(a[k].hi, a[k].lo);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          ff t = {red[k].x, red[k].y};
-          for (int w = 1; w < nwarp; ++w) t = ff_add(t, ff{red[w * MD_NPART + k].x, red[w * MD_NPART + k].y});
-          acc[k] = (double)t.hi + (double)t.lo;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-      for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
-        const double* q = part + (u0 + t) * MD_NPART;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] += q[k];
-      }
+    for (int k = 0; k < 6; ++k) {
+      a[k] = warp_sum_ff(a[k]);
+      if (lane == 0) red[warp * MD_NPART + k] = make_float2(a[k].hi, a[k].lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        acc[k] = warp_sum(acc[k]);
-        if (lane == 0) sh.red[warp][k] = acc[k];
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          double t = sh.red[0][k];
-          for (int w = 1; w < nwarp; ++w) t += sh.red[w][k];
-          acc[k] = t;
-        }
+        ff t = {red[k].x, red[k].y};
+        for (int w = 1; w < nwarp; ++w) t = ff_add(t, ff{red[w * MD_NPART + k].x, red[w * MD_NPART + k].y});
+        acc[k] = (double)t.hi + (double)t.lo;
       }
     }
-    if (threadIdx.x == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+    for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+      const double* q = part + (u0 + t) * MD_NPART;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += q[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      acc[k] = warp_sum(acc[k]);
+      if (lane == 0) sh.red[warp][k] = acc[k];
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double t = sh.red[0][k];
+        for (int w = 1; w < nwarp; ++w) t += sh.red[w][k];
+        acc[k] = t;
+      }
+    }
   }
+  __syncthreads();
+}
+
+// Per-replica totals of the partial records (upt records per tile) and the
+// scalar updates of `mode`. Replicas of at most red_tiles tiles: one CTA
+// per replica. Larger ones (p.red2): chunks of red_tiles tiles are summed
+// by separate CTAs, then, after a grid barrier, one CTA per replica adds its
+// chunk sums in chunk order. Both orders are fixed, so results are
+// reproducible. Returns false after a barrier timeout.
+template <bool MIX>
+__device__ bool reduce_phase(const KParams& p, Shared& sh, const double* part, int upt, int mode, int64_t step,
+                             bool log_now, int64_t log_idx) {
+  const bool nh = (p.kind == MD_KIND_NH || p.kind == MD_KIND_NH_EXACT) && p.op == MD_OP_STEPS;
+  double acc[6];
+  if (!p.red2) {
+    for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
+      RepDev& R = p.reps[r];
+      sum_records<MIX>(sh, part, (int64_t)R.tile0 * upt, (int64_t)R.ntiles * upt, acc);
+      if (threadIdx.x == 0) reduce_scalars(p, R, r, acc, mode, step, log_now, log_idx, nh);
+      __syncthreads();
+    }
+    return true;
+  }
+  for (int64_t g = blockIdx.x; g < p.nred; g += gridDim.x) {
+    const int2 rc = p.redmap[g];
+    const RepDev& R = p.reps[rc.x];
+    const int t0 = rc.y * p.red_tiles;
+    const int nt = min(p.red_tiles, R.ntiles - t0);
+    sum_records<MIX>(sh, part, (int64_t)(R.tile0 + t0) * upt, (int64_t)nt * upt, acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p.redpart[g * MD_NPART + k] = acc[k];
+    }
+  }
+  if (grid_sync(p, sh, 17) < 0) return false;
+  for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int2 rr = p.redrep[r];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+      for (int c = 0; c < rr.y; ++c) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += p.redpart[(int64_t)(rr.x + c) * MD_NPART + k];
+      }
+      reduce_scalars(p, p.reps[r], r, acc, mode, step, log_now, log_idx, nh);
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
@@ -1541,7 +1580,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       // then centre and rescale (steps 1-4 of Sec. "Statistical temperature bath")
       resample_draw_phase<MIX>(p, 0, p.part[0]);
       if ((fl = grid_sync(p, sh, 2)) < 0) return;
-      reduce_phase<MIX>(p, sh, p.part[0], 1, RED_RESAMPLE, step0, false, 0);
+      if (!reduce_phase<MIX>(p, sh, p.part[0], 1, RED_RESAMPLE, step0, false, 0)) return;
       if ((fl = grid_sync(p, sh, 3)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, false, step0);
       finish(false, fvalid);
@@ -1550,7 +1589,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     const bool pairs = !fvalid || p.op == MD_OP_FORCES;
     force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], pairs, true, true, step0);
     if ((fl = grid_sync(p, sh, 4)) < 0) return;
-    reduce_phase<MIX>(p, sh, p.part[0], p.T, pairs ? RED_FORCES : RED_KE, step0, false, 0);
+    if (!reduce_phase<MIX>(p, sh, p.part[0], p.T, pairs ? RED_FORCES : RED_KE, step0, false, 0)) return;
     if ((fl = grid_sync(p, sh, 5)) < 0) return;
     if (p.op == MD_OP_FORCES || p.nsteps == 0) { finish(false, 1); return; }
     drift_phase<MIX>(p, cur, nh, false, true, step0 + 1);
@@ -1585,7 +1624,8 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     if ((fl = grid_sync(p, sh, 10)) < 0) return;
     if (fuse) cur ^= 1;
     now_drifted = fuse;
-    if (need_red) reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx);
+    if (need_red && !reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx))
+      return;
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
@@ -1599,7 +1639,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       double* part2 = p.part[(step & 1) ^ 1];
       resample_draw_phase<MIX>(p, (uint64_t)(step / p.nstep_boltz), part2);
       if ((fl = grid_sync(p, sh, 14)) < 0) return;
-      reduce_phase<MIX>(p, sh, part2, 1, RED_RESAMPLE, step, log_now, lidx);
+      if (!reduce_phase<MIX>(p, sh, part2, 1, RED_RESAMPLE, step, log_now, lidx)) return;
       if ((fl = grid_sync(p, sh, 15)) < 0) return;
       drift_phase<MIX>(p, cur, false, true, !last, step + 1);
       if (!last) { cur ^= 1; now_drifted = true; }

@@ -199,6 +199,41 @@ def test_nose_hoover_100_steps(prec, kind):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("red_tiles", ["3", "16"])
+def test_two_level_reductions(prec, red_tiles, monkeypatch):
+    """Replicas larger than one reduction chunk are reduced in two levels (chunk sums by separate CTAs,
+    then one CTA per replica). Shrinking the chunk to 3 or 16 tiles puts an N = 1000 system (32 tiles)
+    on that path: Nose-Hoover (a reduction every step, xi fed back into the dynamics) and the
+    resampling bath follow the oracle as closely as on the one-level path, and the trajectory is
+    reproducible bitwise."""
+    monkeypatch.setenv("KAMD_RED_TILES", red_tiles)
+    pos, vel, types, L = melted(1000, 32, nsteps=200)
+    T, tau, n = 0.8, 0.5, 1000
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 60, kind=oracle.NOSE_HOOVER, T_target=T,
+                     Q=3 * n * T * tau * tau, log_every=1)
+    runs = []
+    for _ in range(2):
+        with make_system(n, L, types, prec) as s:
+            s.set_state(pos, vel)
+            log = s.step_nvt(0.005, 60, T, kind=kamd.MD_NVT_NOSE_HOOVER, param=tau, log_every=1)
+            runs.append((log, s.get_state()[0]))
+    log = runs[0][0]
+    tol = 1e-10 if prec == "fp64" else TOL_E["mixed"]
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= tol
+    assert thermo_rel(log, ref["thermo"], "h_nh", 6, n=n) <= tol
+    xi_g, xi_r = log["xi"][:, 0], ref["thermo"][:, 7]
+    assert np.max(np.abs(xi_g - xi_r)) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(xi_r))
+    assert np.array_equal(runs[0][1], runs[1][1])
+    ref_rs = oracle.run(pos, vel, types, ka_params(), L, 0.005, 20, kind=oracle.RESAMPLE, T_target=0.5,
+                        nstep_boltz=10, seed=78, log_every=1)
+    with make_system(n, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nvt(0.005, 20, 0.5, kind=kamd.MD_NVT_RESAMPLE, param=10, seed=78, log_every=1)
+    assert abs(log["T"][9, 0] - 0.5) < 1e-12 and abs(log["T"][19, 0] - 0.5) < 1e-12
+    assert thermo_rel(log, ref_rs["thermo"], "etot_per_n", 4) <= tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_resample_bath(prec):
     pos, vel, types, L = melted(1000, 33, nsteps=100)
     ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 40, kind=oracle.RESAMPLE, T_target=0.5, nstep_boltz=10,
@@ -247,7 +282,13 @@ def test_deterministic_bitwise(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_batch_replicas_equal_standalone_runs(prec):
+@pytest.mark.parametrize("red_tiles", [None, "16"], ids=["one-level", "two-level"])
+def test_batch_replicas_equal_standalone_runs(prec, red_tiles, monkeypatch):
+    """Every replica of a batch is bitwise equal to its stand-alone run, also when the batch reduces in
+    two levels (chunks of 16 tiles: the 1000- and 2000-particle replicas span several chunks, the
+    others one) while a small stand-alone replica reduces in one."""
+    if red_tiles is not None:
+        monkeypatch.setenv("KAMD_RED_TILES", red_tiles)
     ns = [250, 1000, 500, 2000]
     Ts = [0.6, 1.2, 0.9, 2.0]
     cfg = [melted(n, 60 + k, nsteps=50) for k, n in enumerate(ns)]
