@@ -334,7 +334,7 @@ def main():
         t4 = args.tuning.split(",")
         s.set_tuning(threads_per_atom=int(t4[0]), block_size=int(t4[1]), skin=float(t4[2]), skin_outer=float(t4[3]))
     elif not args.no_autotune:
-        s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 20)
+        s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 60)
     tuning = s.tuning
     if dist:
         dist.barrier()

@@ -487,9 +487,9 @@ int list_capacity(const md_system* s) {
   return cap;
 }
 
-// List-build groups: as many neighbouring cells per CTA (1, 2 or 4 as
-// 1x1x1, 2x1x1, 2x2x1) as keep the CTA's threads busy at T threads per
-// particle. KAMD_LIST_GROUP (1, 2 or 4) overrides the choice.
+// List-build groups: as many neighbouring cells per CTA (1, 2, 4 or 8 as
+// 1x1x1, 2x1x1, 2x2x1, 2x2x2) as keep the CTA's threads busy at T threads
+// per particle. KAMD_LIST_GROUP (1, 2, 4 or 8) overrides the choice.
 void choose_groups(md_system* s) {
   double occ = 0.0;
   for (int r = 0; r < s->nrep; ++r) {
@@ -503,15 +503,15 @@ void choose_groups(md_system* s) {
     // 10 % headroom: a group whose particles overflow the CTA needs a second,
     // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2)
     const double fit = 0.9 * (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
-    g = fit >= 4.0 ? 4 : (fit >= 2.0 ? 2 : 1);
+    g = fit >= 8.0 ? 8 : (fit >= 4.0 ? 4 : (fit >= 2.0 ? 2 : 1));
   }
   if (const char* e = std::getenv("KAMD_LIST_GROUP")) {
     const int v = std::atoi(e);
-    if (v == 1 || v == 2 || v == 4) g = v;
+    if (v == 1 || v == 2 || v == 4 || v == 8) g = v;
   }
   s->gx = g >= 2 ? 2 : 1;
   s->gy = g >= 4 ? 2 : 1;
-  s->gz = 1;
+  s->gz = g >= 8 ? 2 : 1;
 }
 
 // Staging area of the list build: the candidates of the cells around one
@@ -572,22 +572,26 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
       for (int k = 0; k < ng; ++k) grp.push_back(make_int2(r, k));
     }
     s->ngroups = (int64_t)grp.size();
-    // two-level reductions once a replica spans more than red_tiles tiles
-    // (KAMD_RED_TILES overrides the chunk size, for tests of that path)
+    // two-level reductions (chunks of red_tiles tiles) once a replica spans
+    // more than 4 chunks: below that, one CTA per replica is as fast and, in
+    // NVE, its reduction overlaps the next step instead of adding a barrier.
+    // KAMD_RED_TILES sets the chunk and the threshold to the same value, for
+    // tests of that path.
     s->red_tiles = MD_RED_TILES;
+    int threshold = 4 * MD_RED_TILES;
     if (const char* e = std::getenv("KAMD_RED_TILES")) {
       const int v = std::atoi(e);
-      if (v >= 1) s->red_tiles = v;
+      if (v >= 1) s->red_tiles = threshold = v;
     }
     std::vector<int2> rmap, rrep;
-    int maxch = 1;
+    int maxtiles = 0;
     for (int r = 0; r < s->nrep; ++r) {
       const int nch = (s->reps[r].ntiles + s->red_tiles - 1) / s->red_tiles;
       rrep.push_back(make_int2((int)rmap.size(), nch));
       for (int c = 0; c < nch; ++c) rmap.push_back(make_int2(r, c));
-      maxch = std::max(maxch, nch);
+      maxtiles = std::max(maxtiles, s->reps[r].ntiles);
     }
-    s->red2 = maxch > 1 ? 1 : 0;
+    s->red2 = maxtiles > threshold ? 1 : 0;
     s->nred = (int64_t)rmap.size();
     dfree(s->d_redmap);
     dfree(s->d_redrep);

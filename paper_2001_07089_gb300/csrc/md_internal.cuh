@@ -31,7 +31,7 @@
 #define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
 #define MD_UNION_MAX 64     // staged cells of one list-build group: (GX+2)(GY+2)(GZ+2) <= 4*4*4
 #define MD_ROWS_MAX 4       // (y, z) rows of cells in one list-build group: GY*GZ <= 4
-#define MD_RED_TILES 1024   // tiles per chunk of the two-level per-replica reduction (default)
+#define MD_RED_TILES 256    // tiles per chunk of the two-level per-replica reduction (default)
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
 
 // pending/commit flag bits (grid-uniform decisions)
@@ -124,7 +124,7 @@ struct KParams {
   int ntiles;
   int T;               // lanes per particle
   int maxrows;         // list entries per column (capacity per particle = maxrows*T), a multiple of 4
-  int gx, gy, gz;      // cells per list-build group along x, y, z (1 or 2; gy*gz <= MD_ROWS_MAX)
+  int gx, gy, gz;      // cells per list-build group along x, y, z (1 or 2 each)
   int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps
@@ -188,7 +188,7 @@ struct KParams {
   int32_t* chunk;      // per-chunk cell-count sums of the cell scan (MD_SCAN_CHUNK cells each)
   int32_t* cta_sm;     // SM id of each CTA of the current launch
   const int2* grp;     // list-build groups: (replica, group index inside the replica)
-  int red2;            // 1: reductions in two levels (some replica has more than red_tiles tiles)
+  int red2;            // 1: reductions in two levels (some replica has more than 4 chunks)
   int red_tiles;       // tiles per reduction chunk
   int64_t nred;        // reduction chunks over all replicas
   const int2* redmap;  // chunk -> (replica, chunk index inside the replica)

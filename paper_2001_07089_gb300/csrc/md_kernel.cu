@@ -554,6 +554,26 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
 
 // ------------------------------------------------------------------ prune
 
+// Accepted entries pass through a 4-deep shift register (b1, b2, b3 plus the
+// new one); every fourth entry completes a quad, stored with one 16-byte store.
+__device__ __forceinline__ void list_push(int32_t* col, int gsz, int maxrows, int& k, int& b1, int& b2, int& b3,
+                                          int j) {
+  if ((k & 3) == 3 && k < maxrows)
+    *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = make_int4(b1, b2, b3, j);
+  b1 = b2;
+  b2 = b3;
+  b3 = j;
+  ++k;
+}
+
+// Store the last, partial quad of a column (k % 4 entries in b1..b3).
+__device__ __forceinline__ void list_flush(int32_t* col, int gsz, int maxrows, int k, int b1, int b2, int b3) {
+  const int r = k & 3;
+  if (r == 0 || k - r >= maxrows) return;
+  const int4 v = r == 1 ? make_int4(b3, 0, 0, 0) : (r == 2 ? make_int4(b2, b3, 0, 0) : make_int4(b1, b2, b3, 0));
+  *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = v;
+}
+
 // Inner list from the outer one: every lane keeps, in order, the entries of
 // its outer column that now lie within r_c,ab + skin, and the particle's
 // position becomes the reference of the next prune trigger. A replica is
@@ -586,6 +606,7 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
     int* li = p.nbr_in + off;
     const int cnt = p.nnb[i * T + s];
     int k = 0;
+    int b1 = 0, b2 = 0, b3 = 0;  // quad shift register of the list writer
     if constexpr (MIX) {
       const uint4* __restrict__ pq = p.pq[cur];
       const uint4 pi = pq[i];
@@ -597,10 +618,8 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
         const float dx = (float)(int)(pi.x - pj.x) * sc;
         const float dy = (float)(int)(pi.y - pj.y) * sc;
         const float dz = (float)(int)(pi.z - pj.z) * sc;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj.w]) {
-          li[list_at(0, k, gsz)] = j;
-          ++k;
-        }
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj.w])
+          list_push(li, gsz, p.maxrows, k, b1, b2, b3, j);
       }
       if (s == 0) p.xbq_in[i] = pi;
     } else {
@@ -615,13 +634,12 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
         if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
         if (dy > hL) dy -= L; else if (dy < -hL) dy += L;
         if (dz > hL) dz -= L; else if (dz < -hL) dz += L;
-        if (dx * dx + dy * dy + dz * dz < sh.rli2d[tb + (int)pj.w]) {
-          li[list_at(0, k, gsz)] = j;
-          ++k;
-        }
+        if (dx * dx + dy * dy + dz * dz < sh.rli2d[tb + (int)pj.w])
+          list_push(li, gsz, p.maxrows, k, b1, b2, b3, j);
       }
       if (s == 0) p.xbd_in[i] = pi;
     }
+    list_flush(li, gsz, p.maxrows, k, b1, b2, b3);
     p.nnb_in[i * T + s] = k;
   }
 }
@@ -744,8 +762,8 @@ __device__ void sum_records(Shared& sh, const double* part, int64_t u0, int64_t 
 }
 
 // Per-replica totals of the partial records (upt records per tile) and the
-// scalar updates of `mode`. Replicas of at most red_tiles tiles: one CTA
-// per replica. Larger ones (p.red2): chunks of red_tiles tiles are summed
+// scalar updates of `mode`. One CTA per replica, unless some replica spans
+// more than four chunks (p.red2): then chunks of red_tiles tiles are summed
 // by separate CTAs, then, after a grid barrier, one CTA per replica adds its
 // chunk sums in chunk order. Both orders are fixed, so results are
 // reproducible. Returns false after a barrier timeout.
@@ -775,17 +793,12 @@ __device__ bool reduce_phase(const KParams& p, Shared& sh, const double* part, i
     }
   }
   if (grid_sync(p, sh, 17) < 0) return false;
+  // level 2: one CTA per replica sums the replica's chunk sums as FP64
+  // records (thread-strided, warp trees, warps in order: a fixed order)
   for (int r = blockIdx.x; r < p.nrep; r += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const int2 rr = p.redrep[r];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-      for (int c = 0; c < rr.y; ++c) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] += p.redpart[(int64_t)(rr.x + c) * MD_NPART + k];
-      }
-      reduce_scalars(p, p.reps[r], r, acc, mode, step, log_now, log_idx, nh);
-    }
+    const int2 rr = p.redrep[r];
+    sum_records<false>(sh, p.redpart, rr.x, rr.y, acc);
+    if (threadIdx.x == 0) reduce_scalars(p, p.reps[r], r, acc, mode, step, log_now, log_idx, nh);
   }
   __syncthreads();
   return true;
@@ -889,26 +902,6 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
 // particle itself is excluded (own_q) and the entry is stored.
 // REL: staged FP32 coordinates relative to the group's reference particle;
 // otherwise staged fixed-point words and exact integer differences.
-// Accepted entries pass through a 4-deep shift register (b1, b2, b3 plus the
-// new one); every fourth entry completes a quad, stored with one 16-byte store.
-__device__ __forceinline__ void list_push(int32_t* col, int gsz, int maxrows, int& k, int& b1, int& b2, int& b3,
-                                          int j) {
-  if ((k & 3) == 3 && k < maxrows)
-    *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = make_int4(b1, b2, b3, j);
-  b1 = b2;
-  b2 = b3;
-  b3 = j;
-  ++k;
-}
-
-// Store the last, partial quad of a column (k % 4 entries in b1..b3).
-__device__ __forceinline__ void list_flush(int32_t* col, int gsz, int maxrows, int k, int b1, int b2, int b3) {
-  const int r = k & 3;
-  if (r == 0 || k - r >= maxrows) return;
-  const int4 v = r == 1 ? make_int4(b3, 0, 0, 0) : (r == 2 ? make_int4(b2, b3, 0, 0) : make_int4(b1, b2, b3, 0));
-  *reinterpret_cast<int4*>(col + (int64_t)(k >> 2) * 4 * gsz) = v;
-}
-
 // Distance^2 of staged candidate q from the particle (mixed path); *w gets
 // the candidate's (type << 30) | slot word.
 template <bool REL>
@@ -1259,7 +1252,10 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAnd(&p.ctl->pending, ~MD_FLAG_REBUILD);
   const int nchunks = (int)((p.ncells + MD_SCAN_CHUNK - 1) / MD_SCAN_CHUNK);
   const int cpt = MD_SCAN_CHUNK / (int)blockDim.x;  // cells per thread in a chunk (<= 8)
-  for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
+  // a single chunk (up to MD_SCAN_CHUNK cells): the last CTA computes the
+  // replica bases and scans the chunk itself, with no barrier in between
+  const bool one = nchunks <= 1;
+  for (int k = one ? nchunks : (int)blockIdx.x; k < nchunks; k += gridDim.x) {
     const int64_t c0 = (int64_t)k * MD_SCAN_CHUNK;
     int sum = 0;
     for (int u = 0; u < cpt; ++u) {
@@ -1285,8 +1281,10 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
       carry += total;
     }
   }
-  f = grid_sync(p, sh, 109);
-  if (f < 0) return false;
+  if (!one) {
+    f = grid_sync(p, sh, 109);
+    if (f < 0) return false;
+  }
   // B2b: chunk base (sum of the earlier chunks), scan inside the chunk, and
   // cell start = replica offset + (global prefix - replica base). Cells of
   // replicas that do not rebuild keep their ranges.
@@ -1298,7 +1296,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
     R.rebuild_epoch = epoch;
     if (R.nc > 0) p.cstart[R.cs0 + R.nc * R.nc * R.nc] = (int)(R.off + R.n);
   }
-  for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
+  for (int k = one ? (blockIdx.x == gridDim.x - 1 ? 0 : nchunks) : (int)blockIdx.x; k < nchunks; k += gridDim.x) {
     int part = 0;
     for (int t = threadIdx.x; t < k; t += blockDim.x) part += p.chunk[t];
     int base;

@@ -88,13 +88,13 @@ def test_forces_32k_tiled_melt(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("group", ["1", "2", "4"])
+@pytest.mark.parametrize("group", ["1", "2", "4", "8"])
 @pytest.mark.parametrize("n,tile", [(1000, 1), (4000, 1), (4000, 2)], ids=["1000", "4000", "32000-tiled"])
 def test_list_build_every_group_shape(prec, group, n, tile, monkeypatch):
-    """The list build works on groups of 1, 2 or 4 cells (1x1x1, 2x1x1, 2x2x1). Every shape, on boxes
-    of 3 cells per edge (exact fixed-point test), 5 (FP32 relative coordinates for single cells,
-    exact for groups) and 10 (relative coordinates for every shape), gives the oracle's forces with
-    every lane split."""
+    """The list build works on groups of 1, 2, 4 or 8 cells (1x1x1, 2x1x1, 2x2x1, 2x2x2). Every shape,
+    on boxes of 3 cells per edge (exact fixed-point test), 5 (FP32 relative coordinates for single
+    cells, exact for groups) and 10 (relative coordinates for every shape), gives the oracle's forces
+    with every lane split."""
     pos, vel, types, L = melted(n, 23 if n == 4000 else 22, nsteps=200)
     if tile > 1:
         shifts = np.array([[i, j, k] for i in range(tile) for j in range(tile) for k in range(tile)], dtype=float) * L
