@@ -126,9 +126,9 @@ def drift_per_tau(log, dt):
 
 
 WORKLOADS = {
-    "ka32k": dict(kind="single", n=32000, seed=2, T0=2.0, T=0.8, setup_nvt=2000, timed="nve",
+    "ka32k": dict(kind="single", n=32000, seed=2, T0=2.0, T=0.8, setup_nvt=2000, timed="nve", skin=0.3,
                   desc="ka32k: Kob-Andersen 80:20, N=32000, rho=1.2, L=29.876, lattice+0.05 jitter at T=2.0, "
-                       "2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + Verlet list skin 0.3 "
+                       "2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + Verlet list, force-list skin 0.3 (any outer list autotuned) "
                        "rebuilt on device; one bench step = 100 MD steps"),
     "ka1m": dict(kind="single", n=1_000_000, seed=3, T0=0.5, T=0.5, setup_nvt=200, timed="nvt",
                  desc="ka1m: Kob-Andersen 80:20, N=10^6, rho=1.2, L=94.104, 100^3 lattice+0.05 jitter at T=0.5, "
@@ -334,7 +334,8 @@ def main():
         t4 = args.tuning.split(",")
         s.set_tuning(threads_per_atom=int(t4[0]), block_size=int(t4[1]), skin=float(t4[2]), skin_outer=float(t4[3]))
     elif not args.no_autotune:
-        s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 60)
+        # the configuration's force-list skin (ka32k: 0.3) is kept; the rest is searched
+        s.autotune(wl.DT, probe_steps=200 if n_sys < 200000 else 60, skin=wk.get("skin"))
     tuning = s.tuning
     if dist:
         dist.barrier()
@@ -370,7 +371,7 @@ def main():
     if rank == 0 and k64 > 0:
         s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk)
         if not args.no_autotune:
-            s64.autotune(wl.DT, probe_steps=50)
+            s64.autotune(wl.DT, probe_steps=50, skin=wk.get("skin"))
         t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
         d64, f64 = drift_per_tau(log64, wl.DT) if wk["timed"] == "nve" else (None, None)
         fp64 = {"value": n_sys * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,

@@ -232,6 +232,15 @@ md_status md_get_tuning(const md_system* sys, md_tuning* t);
 md_status md_autotune(md_system* sys, double dt, int64_t probe_steps, md_tuning* best,
                       double* seconds_per_step);
 
+/*
+ * md_autotune_skin: as md_autotune, but the force list's skin stays `skin`
+ * (for a configuration that prescribes it); threads_per_atom, block_size and
+ * the outer list's skin (skin, skin + 0.3, + 0.5, + 0.7) are searched.
+ * MD_ERR_INVALID_ARG unless 0.05 <= skin < 2. (The paper has no counterpart.)
+ */
+md_status md_autotune_skin(md_system* sys, double dt, int64_t probe_steps, double skin, md_tuning* best,
+                           double* seconds_per_step);
+
 /* md_get_info: counters and sizes (synchronises the stream). */
 md_status md_get_info(md_system* sys, md_info* info);
 

@@ -47,15 +47,18 @@ def store(key: str, tuning: dict, seconds_per_step: float, path: str = DEFAULT_C
 
 
 def tune(system, dt: float, gpu_name: str, probe_steps: int = 200, path: str = DEFAULT_CACHE,
-         refresh: bool = False) -> dict:
-    """Apply the cached tuning for this kind of system, or run md_autotune and cache it."""
+         refresh: bool = False, skin=None) -> dict:
+    """Apply the cached tuning for this kind of system, or run md_autotune (md_autotune_skin when
+    `skin` fixes the force list's skin) and cache it."""
     key = cache_key(gpu_name, system.precision, system.n_per, system.L_per)
+    if skin is not None:
+        key += f"|skin{skin:g}"
     entry = None if refresh else load(path).get(key)
     if entry is not None:
         t = entry["tuning"]
         system.set_tuning(threads_per_atom=t["threads_per_atom"], block_size=t["block_size"], skin=t["skin"],
                           skin_outer=t["skin_outer"])
         return t
-    t, sec = system.autotune(dt, probe_steps)
+    t, sec = system.autotune(dt, probe_steps) if skin is None else system.autotune(dt, probe_steps, skin=skin)
     store(key, t, sec, path)
     return t

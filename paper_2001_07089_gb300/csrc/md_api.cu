@@ -1334,7 +1334,10 @@ md_status md_set_tuning(md_system* s, const md_tuning* t) {
   return MD_OK;
 }
 
-md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* best, double* seconds_per_step) {
+// fixed_skin > 0: the force list's skin stays fixed_skin and only the outer
+// skin is searched; otherwise both are.
+static md_status autotune_impl(md_system* s, double dt, int64_t probe_steps, double fixed_skin, md_tuning* best,
+                               double* seconds_per_step) {
   if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
   if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
   if (!(dt > 0) || probe_steps < 1) return fail(s, MD_ERR_INVALID_ARG, "dt > 0 and probe_steps >= 1 required");
@@ -1351,6 +1354,9 @@ md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* b
   const int64_t saved_step = s->ctl.step;
   const md_tuning start = s->tun;
   md_tuning bt = start;
+  // starting skins of the first search stage
+  const double s0 = fixed_skin > 0 ? fixed_skin : start.skin;
+  const double so0 = fixed_skin > 0 ? fixed_skin : start.skin_outer;
   float bms = 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1376,18 +1382,26 @@ md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* b
   const int Ts[4] = {1, 2, 4, 8};
   const int Bs[3] = {128, 256, 512};
   // (skin, skin_outer); equal values mean one list without pruning
-  const double Ss[9][2] = {{0.2, 0.2}, {0.3, 0.3}, {0.4, 0.4}, {0.2, 0.5}, {0.2, 0.7},
-                           {0.3, 0.6}, {0.3, 0.8}, {0.3, 1.0}, {0.4, 0.9}};
+  const double Sfree[9][2] = {{0.2, 0.2}, {0.3, 0.3}, {0.4, 0.4}, {0.2, 0.5}, {0.2, 0.7},
+                              {0.3, 0.6}, {0.3, 0.8}, {0.3, 1.0}, {0.4, 0.9}};
+  double Ss[9][2];
+  int nS = 0;
+  if (fixed_skin > 0) {
+    const double extra[4] = {0.0, 0.3, 0.5, 0.7};
+    for (int k = 0; k < 4; ++k) { Ss[nS][0] = fixed_skin; Ss[nS][1] = fixed_skin + extra[k]; ++nS; }
+  } else {
+    for (int k = 0; k < 9; ++k) { Ss[nS][0] = Sfree[k][0]; Ss[nS][1] = Sfree[k][1]; ++nS; }
+  }
   // coordinate search: lanes x block size at the starting skins, then the
   // skins at the best of those, then lanes x block size again at the best skins
   for (int ti = 0; ti < 4; ++ti)
-    for (int bi = 0; bi < 3; ++bi) probe(md_tuning{Ts[ti], Bs[bi], start.skin, start.skin_outer});
+    for (int bi = 0; bi < 3; ++bi) probe(md_tuning{Ts[ti], Bs[bi], s0, so0});
   const md_tuning b1 = bt;
-  for (int si = 0; si < 9; ++si)
-    if (!(Ss[si][0] == start.skin && Ss[si][1] == start.skin_outer))
+  for (int si = 0; si < nS; ++si)
+    if (!(Ss[si][0] == s0 && Ss[si][1] == so0))
       probe(md_tuning{b1.threads_per_atom, b1.block_size, Ss[si][0], Ss[si][1]});
   const md_tuning b2 = bt;
-  if (!(b2.skin == start.skin && b2.skin_outer == start.skin_outer))
+  if (!(b2.skin == s0 && b2.skin_outer == so0))
     for (int ti = 0; ti < 4; ++ti)
       for (int bi = 0; bi < 3; ++bi)
         if (!(Ts[ti] == b2.threads_per_atom && Bs[bi] == b2.block_size))
@@ -1427,6 +1441,16 @@ md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* b
   if (best) *best = bt;
   if (seconds_per_step) *seconds_per_step = (double)bms * 1e-3 / (double)probe_steps;
   return MD_OK;
+}
+
+md_status md_autotune(md_system* s, double dt, int64_t probe_steps, md_tuning* best, double* seconds_per_step) {
+  return autotune_impl(s, dt, probe_steps, -1.0, best, seconds_per_step);
+}
+
+md_status md_autotune_skin(md_system* s, double dt, int64_t probe_steps, double skin, md_tuning* best,
+                           double* seconds_per_step) {
+  if (!(skin >= 0.05) || !(skin < 2.0)) return fail(s, MD_ERR_INVALID_ARG, "skin must be in [0.05, 2)");
+  return autotune_impl(s, dt, probe_steps, skin, best, seconds_per_step);
 }
 
 md_status md_get_tuning(const md_system* s, md_tuning* t) {

@@ -32,6 +32,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
 
 EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_set_tuning", "md_get_tuning", "md_autotune",
+            "md_autotune_skin",
             "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_forces_noalloc", "md_last_error",
             "md_destroy")
 
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
             "md_set_tuning": [P, ctypes.POINTER(md_tuning)],
             "md_get_tuning": [P, ctypes.POINTER(md_tuning)],
             "md_autotune": [P, dbl, i64, ctypes.POINTER(md_tuning), ctypes.POINTER(dbl)],
+            "md_autotune_skin": [P, dbl, i64, dbl, ctypes.POINTER(md_tuning), ctypes.POINTER(dbl)],
             "md_get_info": [P, ctypes.POINTER(md_info)],
             "md_count_pairs": [P, ctypes.POINTER(i64)],
             "md_selftest_barrier": [P, dbl],
@@ -215,6 +217,14 @@ def md_autotune(h, dt, probe_steps):
     t = md_tuning()
     sec = ctypes.c_double()
     _check(load().md_autotune(h, float(dt), int(probe_steps), ctypes.byref(t), ctypes.byref(sec)), h)
+    return t, sec.value
+
+
+def md_autotune_skin(h, dt, probe_steps, skin):
+    t = md_tuning()
+    sec = ctypes.c_double()
+    _check(load().md_autotune_skin(h, float(dt), int(probe_steps), float(skin), ctypes.byref(t), ctypes.byref(sec)),
+           h)
     return t, sec.value
 
 
@@ -355,8 +365,12 @@ class System:
         so = skin_outer if skin_outer is not None else max(cur["skin_outer"], sk + 0.4)
         md_set_tuning(self._h, threads_per_atom or cur["threads_per_atom"], block_size or cur["block_size"], sk, so)
 
-    def autotune(self, dt, probe_steps=100):
-        t, sec = md_autotune(self._h, dt, probe_steps)
+    def autotune(self, dt, probe_steps=100, skin=None):
+        """Search the launch configuration; with `skin`, the force list's skin stays fixed."""
+        if skin is None:
+            t, sec = md_autotune(self._h, dt, probe_steps)
+        else:
+            t, sec = md_autotune_skin(self._h, dt, probe_steps, skin)
         return {"threads_per_atom": t.threads_per_atom, "block_size": t.block_size, "skin": t.skin,
                 "skin_outer": t.skin_outer}, sec
 

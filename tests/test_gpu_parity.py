@@ -410,3 +410,28 @@ def test_graph_launch_matches_direct_launch(monkeypatch):
     for a, b in zip(runs[0][0], runs[1][0]):
         assert np.array_equal(a, b)
     assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+
+
+@pytest.mark.parametrize("fixed_skin", [None, 0.3], ids=["free", "skin-0.3"])
+def test_autotune_restores_state_and_keeps_parity(fixed_skin):
+    """The autotuner (lanes per particle x CTA size x skins, or with the force-list skin fixed) times
+    short NVE probes on a copy of the state: afterwards the state is the one it started from, the
+    chosen tuning is valid, and the run continues with the oracle's energies."""
+    pos, vel, types, L = melted(4000, 41, nsteps=100)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 40, log_every=1)
+    with make_system(4000, L, types, "mixed") as s:
+        s.set_state(pos, vel)
+        p0, v0, i0 = s.get_state()
+        tun, sec = s.autotune(0.005, probe_steps=10, skin=fixed_skin)
+        p1, v1, i1 = s.get_state()
+        # velocities and images come back exactly; positions pass once more through the 64-bit
+        # fixed-point form, which can move the last bits of a double
+        assert np.array_equal(v0, v1) and np.array_equal(i0, i1)
+        assert np.max(np.abs(p1 - p0)) <= 1e-12 * L
+        assert tun == s.tuning and sec > 0
+        assert tun["threads_per_atom"] in (1, 2, 4, 8) and tun["block_size"] in (128, 256, 512)
+        assert tun["skin_outer"] >= tun["skin"]
+        if fixed_skin is not None:
+            assert tun["skin"] == fixed_skin
+        log = s.step_nve(0.005, 40, log_every=1)
+    assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= TOL_E["mixed"]
