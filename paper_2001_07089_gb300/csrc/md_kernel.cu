@@ -612,14 +612,26 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
       const uint4 pi = pq[i];
       const int tb = (int)pi.w * p.ntypes;
       const float sc = R.fxs;
-      for (int q = 0; q < cnt; ++q) {
-        const int j = lo[list_at(0, q, gsz)];
-        const uint4 pj = pq[j];
-        const float dx = (float)(int)(pi.x - pj.x) * sc;
-        const float dy = (float)(int)(pi.y - pj.y) * sc;
-        const float dz = (float)(int)(pi.z - pj.z) * sc;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj.w])
-          list_push(li, gsz, p.maxrows, k, b1, b2, b3, j);
+      // a quad of outer entries per iteration: one 16-byte index load, issued
+      // a quad ahead, and four position gathers in flight together
+      const int64_t qstride = 4 * (int64_t)gsz;
+      int4 jq = make_int4(0, 0, 0, 0);
+      if (cnt > 0) jq = *reinterpret_cast<const int4*>(lo);
+      for (int q = 0; q < cnt; q += 4) {
+        const int m = min(4, cnt - q);
+        const int j[4] = {jq.x, jq.y, jq.z, jq.w};
+        uint4 pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pj[u] = pq[u < m ? j[u] : j[0]];
+        if (q + 4 < cnt) jq = *reinterpret_cast<const int4*>(lo + (int64_t)((q + 4) >> 2) * qstride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float dx = (float)(int)(pi.x - pj[u].x) * sc;
+          const float dy = (float)(int)(pi.y - pj[u].y) * sc;
+          const float dz = (float)(int)(pi.z - pj[u].z) * sc;
+          if (u < m && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < sh.rli2f[tb + (int)pj[u].w])
+            list_push(li, gsz, p.maxrows, k, b1, b2, b3, j[u]);
+        }
       }
       if (s == 0) p.xbq_in[i] = pi;
     } else {
@@ -1406,6 +1418,9 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
             ((float*)p.t_frc)[cc * nt + d] = fo[cc];
             p.t_img[cc * nt + d] = im[cc];
           }
+          // the gather copy goes straight to its new slot (nothing in this
+          // phase reads it), so the list build need not wait for B5
+          p.pq[cur][d] = make_uint4((uint32_t)(u[0] >> 32), (uint32_t)(u[1] >> 32), (uint32_t)(u[2] >> 32), ty);
         } else {
           const double4_32a x = p.p4[cur][o];
           double v[3], fo[3];
@@ -1427,7 +1442,7 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
   }
   f = grid_sync(p, sh, 104);
   if (f < 0) return false;
-  // B5: copy back, refresh the gather copy
+  // B5: copy back (FP64: positions included, which are also the gather copy)
   for (int64_t i = gtid; i < nt; i += stride) {
     const RepDev& R = p.reps[p.tile_rep[i >> 5]];
     if (i - R.off >= R.n || !R.doing_rebuild || R.nc == 0) continue;
@@ -1449,7 +1464,6 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
         p.frcf[cc * nt + i] = fo[cc];
         p.img[cc * nt + i] = im[cc];
       }
-      p.pq[cur][i] = make_uint4((uint32_t)(u[0] >> 32), (uint32_t)(u[1] >> 32), (uint32_t)(u[2] >> 32), ty);
     } else {
       const double4_32a x = p.t_p4[i];
       double v[3], fo[3];
@@ -1467,8 +1481,13 @@ __device__ bool rebuild(const KParams& p, Shared& sh, int cur, int* fl, int64_t 
     p.gid[i] = gd;
     p.typ[i] = ty;
   }
-  f = grid_sync(p, sh, 105);
-  if (f < 0) return false;
+  // mixed path: B5 and B6 share a phase (B6 reads only the gather copy,
+  // written in B4, and writes only the lists); FP64: B6 reads the positions
+  // that B5 moves back, so a barrier separates them
+  if constexpr (!MIX) {
+    f = grid_sync(p, sh, 105);
+    if (f < 0) return false;
+  }
   // B6: Verlet lists (build_lists)
   build_lists<MIX>(p, sh, cur);
   f = grid_sync(p, sh, 106);
