@@ -361,11 +361,10 @@ __device__ __forceinline__ void pair_mix(const Shared& sh, const uint4& pi, cons
 // latencies overlap.
 template <bool ENERGY>
 __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __restrict__ pq, const int* lp, int gsz,
-                                             int cnt, const uint4& pi, int tb, float sc, float& fx, float& fy,
-                                             float& fz, float& pe, float& vir) {
+                                             int cnt, int4 jq, const uint4& pi, int tb, float sc, float& fx,
+                                             float& fy, float& fz, float& pe, float& vir) {
+  // jq: the column's first quad of indices, loaded by the caller
   const int64_t qstride = 4 * (int64_t)gsz;  // ints between consecutive quads of one column
-  int4 jq = make_int4(0, 0, 0, 0);
-  if (cnt > 0) jq = *reinterpret_cast<const int4*>(lp);
   int q = 0;
   for (; q + 4 <= cnt; q += 4) {
     const uint4 p0 = pq[jq.x], p1 = pq[jq.y], p2 = pq[jq.z], p3 = pq[jq.w];
@@ -421,14 +420,20 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
           fo[c] = p.frcf[c * nt + i];
         }
       }
+      // the first quad of list indices does not depend on the replica either
+      // (slots past a replica's end have empty lists)
+      int4 jq0 = make_int4(0, 0, 0, 0);
+      if (cnt0 > 0) jq0 = *reinterpret_cast<const int4*>(lp);
       const RepDev* R = &p.reps[p.tile_rep[tile]];
       const bool act = (tile - R->tile0) * 32 + a < R->n;
       const int cnt = act ? cnt0 : 0;
       float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, vir = 0.f;
       if (act) {
         const uint4* __restrict__ pq = p.pq[cur];
-        if (energy) lane_sum_mix<true>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
-        else lane_sum_mix<false>(sh, pq, lp, gsz, cnt, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
+        if (energy)
+          lane_sum_mix<true>(sh, pq, lp, gsz, cnt, jq0, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
+        else
+          lane_sum_mix<false>(sh, pq, lp, gsz, cnt, jq0, pi, (int)pi.w * p.ntypes, R->fxs, fx, fy, fz, pe, vir);
       }
       for (int o = T >> 1; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
