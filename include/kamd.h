@@ -91,7 +91,8 @@ typedef struct {
     int32_t grid_blocks;      /* CTAs of the persistent kernel (co-resident) */
     int64_t steps_done;       /* steps advanced since md_create */
     int64_t rebuilds;         /* neighbour-list rebuilds (summed over replicas) */
-    int64_t list_entries;     /* current neighbour-list entries (candidate pairs, full list) */
+    int64_t list_entries;     /* entries of the list the force phase reads (the inner list when
+                                 there are two; candidate pairs, full list) */
     int64_t list_capacity;    /* entries per particle the list can hold */
     int64_t device_bytes;     /* device memory held by the system */
     int32_t all_pairs_replicas; /* replicas too small for cells (list built by all-pairs scan) */

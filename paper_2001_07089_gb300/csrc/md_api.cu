@@ -1473,8 +1473,10 @@ md_status md_get_info(md_system* s, md_info* info) {
     info->all_pairs_replicas += R.nc == 0;
   }
   CK(cudaMemsetAsync(s->d_count, 0, 8, s->stream));
+  // entries of the list the force phase reads: the inner list when there are two
+  const bool dual = s->tun.skin_outer > s->tun.skin;
   k_sum_i32<<<std::max(1, std::min(1024, blocks_for(s->ntot * s->tun.threads_per_atom, 256))), 256, 0, s->stream>>>(
-      s->ntot * s->tun.threads_per_atom, s->d_nnb, s->d_count);
+      s->ntot * s->tun.threads_per_atom, dual ? s->d_nnb_in : s->d_nnb, s->d_count);
   CK(cudaGetLastError());
   unsigned long long entries = 0;
   CK(cudaMemcpyAsync(&entries, s->d_count, 8, cudaMemcpyDeviceToHost, s->stream));
