@@ -236,7 +236,7 @@ md_status md_autotune(md_system* sys, double dt, int64_t probe_steps, md_tuning*
 /*
  * md_autotune_skin: as md_autotune, but the force list's skin stays `skin`
  * (for a configuration that prescribes it); threads_per_atom, block_size and
- * the outer list's skin (skin, skin + 0.3, + 0.5, + 0.7) are searched.
+ * the outer list's skin (skin, skin + 0.3, + 0.5, + 0.7, + 0.9, + 1.1) are searched.
  * MD_ERR_INVALID_ARG unless 0.05 <= skin < 2. (The paper has no counterpart.)
  */
 md_status md_autotune_skin(md_system* sys, double dt, int64_t probe_steps, double skin, md_tuning* best,

@@ -1387,8 +1387,8 @@ static md_status autotune_impl(md_system* s, double dt, int64_t probe_steps, dou
   double Ss[9][2];
   int nS = 0;
   if (fixed_skin > 0) {
-    const double extra[4] = {0.0, 0.3, 0.5, 0.7};
-    for (int k = 0; k < 4; ++k) { Ss[nS][0] = fixed_skin; Ss[nS][1] = fixed_skin + extra[k]; ++nS; }
+    const double extra[6] = {0.0, 0.3, 0.5, 0.7, 0.9, 1.1};
+    for (int k = 0; k < 6; ++k) { Ss[nS][0] = fixed_skin; Ss[nS][1] = fixed_skin + extra[k]; ++nS; }
   } else {
     for (int k = 0; k < 9; ++k) { Ss[nS][0] = Sfree[k][0]; Ss[nS][1] = Sfree[k][1]; ++nS; }
   }
