@@ -3,8 +3,12 @@
 
 Workload (the 32k configuration): lattice + 0.05 jitter start at T = 2.0,
 2000 Nose-Hoover steps to T = 0.8 (set-up, untimed), then NVE at dt = 0.005
-with a cell + Verlet list of skin 0.3 (rebuilt on the device when any
-particle has moved more than skin/2).
+with a cell + Verlet list whose force-list skin is 0.3 (rebuilt on the
+device when any particle has moved more than skin/2; the autotuner may add an
+outer list that the force list is pruned from). Other lines: --workload ka1m
+(10^6 particles, Nose-Hoover at T = 0.5, with the cost of the g(r) and MSD
+calls reported separately), ka8m (8*10^6, quench 2.0 -> 0.45 then NVE, with
+the device footprint), ensemble (512 replicas in one launch).
 
 One bench step = one persistent launch that advances the system 100 MD steps
 (force + velocity Verlet + reductions + every list rebuild the dynamics
@@ -133,6 +137,11 @@ WORKLOADS = {
     "ka1m": dict(kind="single", n=1_000_000, seed=3, T0=0.5, T=0.5, setup_nvt=200, timed="nvt",
                  desc="ka1m: Kob-Andersen 80:20, N=10^6, rho=1.2, L=94.104, 100^3 lattice+0.05 jitter at T=0.5, "
                       "Nose-Hoover NVT at T=0.5 dt=0.005 (200 untimed steps, then timed); one bench step = 100 MD steps"),
+    "ka8m": dict(kind="single", n=8_000_000, seed=5, T0=2.0, T=0.45, setup_nvt=200, pre_nvt=(2.0, 200),
+                 timed="nve",
+                 desc="ka8m: Kob-Andersen 80:20, N=8*10^6, rho=1.2, L=188.207, 200^3 lattice+0.05 jitter at T=2.0, "
+                      "200 Nose-Hoover steps at T=2.0 then an instant quench (200 steps at T=0.45), untimed; then NVE "
+                      "dt=0.005; one bench step = 100 MD steps"),
     "ensemble": dict(kind="ensemble", nrep=512, seed=4, T0=2.0, setup_nvt=200, timed="nvt",
                      desc="ensemble: 512 independent KA replicas in one persistent launch, N per replica uniform "
                           "over {250,500,1000,2000,4000,8000}, rho=1.2, per-replica Nose-Hoover at T uniform in "
@@ -156,8 +165,28 @@ def setup_system(kamd, wl, prec, device, wk=None):
         n = spec.total
         T = spec.T
     s.init_lattice(wk["T0"], 0.05, wk["seed"])
+    if "pre_nvt" in wk:  # a first bath stage before the quench to T
+        T0, k0 = wk["pre_nvt"]
+        s.step_nvt(wl.DT, k0, np.full_like(T, T0), kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
     s.step_nvt(wl.DT, wk["setup_nvt"], T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
     return s, n, T
+
+
+def analysis_cost(torch, s, reps=3):
+    """Wall time of the analysis calls of the 10^6 configuration (partial g(r): 400 bins of 0.01 up to
+    4 sigma; per-type MSD), each a synchronous call through the C ABI, best of `reps`."""
+    out = {}
+    for name, fn in (("rdf_ms", lambda: s.rdf(0.01, 400, reset=True)), ("msd_ms", lambda: s.msd())):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt_ = (time.perf_counter() - t0) * 1e3
+            best = dt_ if best is None else min(best, dt_)
+        out[name] = best
+    return out
 
 
 def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY, step=None):
@@ -356,6 +385,8 @@ def main():
     achieved = flop_step * CHUNK / launch_s / 1e12
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * FP32_LANES_PER_SM * nsm * SM_MAX_MHZ * 1e6 / 1e12
+    analysis = analysis_cost(torch, s) if args.workload == "ka1m" else None
+    device_bytes = info["device_bytes"]
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(3, min(args.steps, 20))
@@ -371,7 +402,7 @@ def main():
     if rank == 0 and k64 > 0:
         s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk)
         if not args.no_autotune:
-            s64.autotune(wl.DT, probe_steps=50, skin=wk.get("skin"))
+            s64.autotune(wl.DT, probe_steps=50 if n_sys < 200000 else 10, skin=wk.get("skin"))
         t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
         d64, f64 = drift_per_tau(log64, wl.DT) if wk["timed"] == "nve" else (None, None)
         fp64 = {"value": n_sys * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
@@ -403,8 +434,12 @@ def main():
         "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.workload, tuning),
+                     "frac_at_measured_clock": (achieved / (peak * clk["sm_mhz"] / SM_MAX_MHZ)
+                                                if clk.get("sm_mhz") else None),
                      "kernel": "md_persistent<mixed> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
+        "analysis_ms": analysis,
+        "device_bytes": device_bytes,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kamd.h"
@@ -94,7 +95,8 @@ struct md_system {
   int64_t rdf_meas = 0;
   double* d_msd_part = nullptr;
   unsigned long long* d_count = nullptr;
-  size_t bytes = 0;
+  size_t bytes = 0;  // device bytes currently held (dalloc/dfree)
+  std::unordered_map<const void*, size_t> alloc_sizes;
   size_t list_bytes = 0;
   unsigned long long timeout_ns = 10ull * 1000 * 1000 * 1000;
   // the persistent launch as an instantiated CUDA graph (one cooperative
@@ -137,14 +139,24 @@ md_status dalloc(md_system* s, T** p, size_t count) {
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) return cuda_fail(s, e, "cudaMalloc");
   s->bytes += count * sizeof(T);
+  s->alloc_sizes[(const void*)*p] = count * sizeof(T);
   e = cudaMemsetAsync(*p, 0, count * sizeof(T), s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemsetAsync");
   return MD_OK;
 }
 
+// Free a device array allocated by dalloc and take its size off the
+// footprint counter (md_get_info's device_bytes).
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+void dfree(md_system* s, T*& p) {
+  if (p) {
+    auto it = s->alloc_sizes.find((const void*)p);
+    if (it != s->alloc_sizes.end()) {
+      s->bytes -= it->second;
+      s->alloc_sizes.erase(it);
+    }
+    cudaFree((void*)p);
+  }
   p = nullptr;
 }
 
@@ -540,13 +552,13 @@ size_t stage_bytes(const md_system* s) { return (size_t)s->stage_cap * (s->mixed
 
 md_status alloc_cells_and_list(md_system* s, int cap_entries) {
   const int T = s->tun.threads_per_atom;
-  dfree(s->d_ccount);
-  dfree(s->d_cstart);
-  dfree(s->d_ccursor);
-  dfree(s->d_chunk);
-  dfree(s->d_nbr);
-  dfree(s->d_nbr_in);
-  dfree(s->d_cell_rep);
+  dfree(s, s->d_ccount);
+  dfree(s, s->d_cstart);
+  dfree(s, s->d_ccursor);
+  dfree(s, s->d_chunk);
+  dfree(s, s->d_nbr);
+  dfree(s, s->d_nbr_in);
+  dfree(s, s->d_cell_rep);
   s->maxrows = ((cap_entries + T - 1) / T + 3) / 4 * 4;  // list layout: whole quads per column
   CKS(dalloc(s, &s->d_cell_rep, (size_t)s->ncells));
   {
@@ -593,9 +605,9 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
     }
     s->red2 = maxtiles > threshold ? 1 : 0;
     s->nred = (int64_t)rmap.size();
-    dfree(s->d_redmap);
-    dfree(s->d_redrep);
-    dfree(s->d_redpart);
+    dfree(s, s->d_redmap);
+    dfree(s, s->d_redrep);
+    dfree(s, s->d_redpart);
     s->d_redmap = nullptr;
     s->d_redrep = nullptr;
     s->d_redpart = nullptr;
@@ -607,7 +619,7 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
       CK(cudaMemcpyAsync(s->d_redrep, rrep.data(), sizeof(int2) * rrep.size(), cudaMemcpyHostToDevice, s->stream));
       CK(cudaStreamSynchronize(s->stream));  // local vectors
     }
-    dfree(s->d_grp);
+    dfree(s, s->d_grp);
     s->d_grp = nullptr;
     CKS(dalloc(s, &s->d_grp, std::max<size_t>(grp.size(), 1)));
     if (!grp.empty()) {
@@ -639,7 +651,7 @@ md_status configure_grid(md_system* s) {
   if (per_sm < 1) return fail(s, MD_ERR_INVALID_ARG, "block size too large for the persistent kernel");
   s->grid = per_sm * s->nsm;
   if (s->grid > s->cta_sm_cap) {
-    dfree(s->d_cta_sm);
+    dfree(s, s->d_cta_sm);
     s->d_cta_sm = nullptr;
     s->cta_sm_cap = 0;
     CKS(dalloc(s, &s->d_cta_sm, (size_t)s->grid));
@@ -866,7 +878,7 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
 
 md_status ensure_thermo(md_system* s, int64_t records) {
   if (records <= s->thermo_cap) return MD_OK;
-  dfree(s->d_thermo);
+  dfree(s, s->d_thermo);
   CKS(dalloc(s, &s->d_thermo, (size_t)records));
   s->thermo_cap = records;
   return MD_OK;
@@ -1260,7 +1272,7 @@ md_status md_rdf(md_system* s, double dr, int64_t nbins, double* g, int reset) {
   for (int r = 0; r < s->nrep; ++r)
     if (dr * nbins > 0.5 * s->L_per[r] * (1 + 1e-12)) return fail(s, MD_ERR_INVALID_ARG, "nbins*dr must be <= L/2");
   if (reset || !s->d_rdf || nbins != s->rdf_nbins || dr != s->rdf_dr) {
-    dfree(s->d_rdf);
+    dfree(s, s->d_rdf);
     CKS(dalloc(s, &s->d_rdf, (size_t)s->nrep * 3 * nbins));
     s->rdf_nbins = nbins;
     s->rdf_dr = dr;
@@ -1348,7 +1360,7 @@ static md_status autotune_impl(md_system* s, double dt, int64_t probe_steps, dou
   CKS(dalloc(s, &saved, 2 * n3));
   CKS(dalloc(s, &saved_img, n3));
   md_status st = md_get_state(s, saved, saved + n3, saved_img, 1);
-  if (st != MD_OK) { dfree(saved); dfree(saved_img); return st; }
+  if (st != MD_OK) { dfree(s, saved); dfree(s, saved_img); return st; }
   CKS(download_reps(s));
   const std::vector<RepDev> saved_reps = s->reps;
   const int64_t saved_step = s->ctl.step;
@@ -1433,9 +1445,8 @@ static md_status autotune_impl(md_system* s, double dt, int64_t probe_steps, dou
   }
   if (st2 == MD_OK) st2 = reset_msd_ref(s);
   cudaStreamSynchronize(s->stream);
-  s->bytes -= (3 * n3) * 8;
-  dfree(saved);
-  dfree(saved_img);
+  dfree(s, saved);
+  dfree(s, saved_img);
   if (st != MD_OK) return st;
   if (st2 != MD_OK) return st2;
   if (best) *best = bt;
@@ -1564,17 +1575,17 @@ void md_destroy(md_system* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   drop_graph(s);
-  dfree(s->d_reps); dfree(s->d_tile_rep); dfree(s->d_ctl);
-  dfree(s->d_pfx); dfree(s->d_pq[0]); dfree(s->d_pq[1]); dfree(s->d_velf); dfree(s->d_frcf); dfree(s->d_xbq);
-  dfree(s->d_xbq_in); dfree(s->d_xbd_in); dfree(s->d_nbr_in); dfree(s->d_nnb_in);
-  dfree(s->d_p4[0]); dfree(s->d_p4[1]); dfree(s->d_veld); dfree(s->d_frcd); dfree(s->d_xbd);
-  dfree(s->d_gid); dfree(s->d_typ); dfree(s->d_img);
-  dfree(s->d_tpfx); dfree(s->d_tp4); dfree(s->d_tvel); dfree(s->d_tfrc); dfree(s->d_tgid); dfree(s->d_ttyp);
-  dfree(s->d_timg);
-  dfree(s->d_cellof); dfree(s->d_cell_rep); dfree(s->d_ccount); dfree(s->d_cstart); dfree(s->d_ccursor); dfree(s->d_chunk); dfree(s->d_cta_sm); dfree(s->d_grp); dfree(s->d_redmap); dfree(s->d_redrep); dfree(s->d_redpart); dfree(s->d_scat);
-  dfree(s->d_nbr); dfree(s->d_nnb); dfree(s->d_part[0]); dfree(s->d_part[1]);
-  dfree(s->d_typ_caller); dfree(s->d_rep_of_caller); dfree(s->d_msd_ref); dfree(s->d_thermo); dfree(s->d_io);
-  dfree(s->d_io_i); dfree(s->d_rdf); dfree(s->d_msd_part); dfree(s->d_count);
+  dfree(s, s->d_reps); dfree(s, s->d_tile_rep); dfree(s, s->d_ctl);
+  dfree(s, s->d_pfx); dfree(s, s->d_pq[0]); dfree(s, s->d_pq[1]); dfree(s, s->d_velf); dfree(s, s->d_frcf); dfree(s, s->d_xbq);
+  dfree(s, s->d_xbq_in); dfree(s, s->d_xbd_in); dfree(s, s->d_nbr_in); dfree(s, s->d_nnb_in);
+  dfree(s, s->d_p4[0]); dfree(s, s->d_p4[1]); dfree(s, s->d_veld); dfree(s, s->d_frcd); dfree(s, s->d_xbd);
+  dfree(s, s->d_gid); dfree(s, s->d_typ); dfree(s, s->d_img);
+  dfree(s, s->d_tpfx); dfree(s, s->d_tp4); dfree(s, s->d_tvel); dfree(s, s->d_tfrc); dfree(s, s->d_tgid); dfree(s, s->d_ttyp);
+  dfree(s, s->d_timg);
+  dfree(s, s->d_cellof); dfree(s, s->d_cell_rep); dfree(s, s->d_ccount); dfree(s, s->d_cstart); dfree(s, s->d_ccursor); dfree(s, s->d_chunk); dfree(s, s->d_cta_sm); dfree(s, s->d_grp); dfree(s, s->d_redmap); dfree(s, s->d_redrep); dfree(s, s->d_redpart); dfree(s, s->d_scat);
+  dfree(s, s->d_nbr); dfree(s, s->d_nnb); dfree(s, s->d_part[0]); dfree(s, s->d_part[1]);
+  dfree(s, s->d_typ_caller); dfree(s, s->d_rep_of_caller); dfree(s, s->d_msd_ref); dfree(s, s->d_thermo); dfree(s, s->d_io);
+  dfree(s, s->d_io_i); dfree(s, s->d_rdf); dfree(s, s->d_msd_part); dfree(s, s->d_count);
   delete s;
 }
 

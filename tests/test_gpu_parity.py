@@ -435,3 +435,23 @@ def test_autotune_restores_state_and_keeps_parity(fixed_skin):
             assert tun["skin"] == fixed_skin
         log = s.step_nve(0.005, 40, log_every=1)
     assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= TOL_E["mixed"]
+
+
+def test_device_footprint_counter_tracks_frees():
+    """md_get_info's device_bytes follows allocations and frees: retuning (which reallocates the lists)
+    and autotuning leave it at the footprint of the final tuning, not the sum of every allocation."""
+    pos, vel, types, L = melted(4000, 42, nsteps=50)
+    with make_system(4000, L, types, "mixed") as s:
+        s.set_state(pos, vel)
+        s.step_nve(0.005, 10)
+        base = s.info()["device_bytes"]
+        for tpa in (1, 2, 4, 8, 4):
+            s.set_tuning(threads_per_atom=tpa)
+            s.step_nve(0.005, 10)
+        again = s.info()["device_bytes"]
+        s.autotune(0.005, probe_steps=5)
+        s.set_tuning(threads_per_atom=4, block_size=256, skin=0.3, skin_outer=0.7)
+        s.step_nve(0.005, 10)
+        after = s.info()["device_bytes"]
+    assert 0 < base < 2 ** 31
+    assert abs(again - base) <= 0.5 * base and abs(after - base) <= 0.5 * base
