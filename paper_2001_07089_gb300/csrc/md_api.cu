@@ -321,74 +321,111 @@ __global__ void k_msd_final(int ntiles, int ntypes, const double* part, double* 
 // Pair-distance histogram of Sec. "Radial distribution function with
 // Python": every unordered pair with r < nbins*dr adds 2 (like) or 1 (unlike)
 // to bin floor(r/dr) of its replica (integer counts; exact, order-free).
+// Mixed path: a conservative FP32 test on the 32-bit gather words rejects the
+// pairs beyond r_max (most candidates); the bin of the others comes from the
+// exact 64-bit positions in FP64, as before. A block whose particles all
+// belong to one replica (and nbins <= RDF_SMEM_BINS) counts into a shared-
+// memory histogram and adds it to the replica's histogram once.
+#define RDF_SMEM_BINS 1024
 __global__ void k_rdf(bool mixed, int64_t ntot, int nbins, double dr, double skin, const RepDev* reps,
                       const int32_t* tile_rep, int cur, const uint4* pq, const uint64_t* pfx, const double4_32a* p4,
                       const uint8_t* typ, const int32_t* cstart, unsigned long long* hist) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ntot) return;
-  const int r = tile_rep[i >> 5];
+  __shared__ unsigned int sh_h[3 * RDF_SMEM_BINS];
+  __shared__ int sh_rep;
+  const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t i = b0 + threadIdx.x;
+  if (threadIdx.x == 0) {
+    const int64_t last = min(b0 + (int64_t)blockDim.x, ntot) - 1;
+    const int r0 = tile_rep[b0 >> 5];
+    sh_rep = (nbins <= RDF_SMEM_BINS && tile_rep[last >> 5] == r0) ? r0 : -1;
+  }
+  __syncthreads();
+  const bool priv = sh_rep >= 0;
+  if (priv)
+    for (int t = threadIdx.x; t < 3 * nbins; t += blockDim.x) sh_h[t] = 0u;
+  __syncthreads();
+  bool act = i < ntot;
+  const int r = act ? tile_rep[i >> 5] : 0;
   const RepDev& R = reps[r];
-  if (i - R.off >= R.n) return;
-  const double rmax = dr * nbins, rmax2 = rmax * rmax;
-  const int ti = typ[i];
-  double xi[3];
-  uint64_t ui[3];
-  for (int c = 0; c < 3; ++c) {
-    if (mixed) ui[c] = pfx[c * ntot + i];
-    else xi[c] = c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z;
-  }
-  const int nc = R.nc;
-  const int layers = nc > 0 ? (int)ceil((rmax + skin) * (1.0 + 1e-6) / (double)R.cellw) : 0;
-  const bool all = nc == 0 || 2 * layers + 1 > nc;
-  int cx = 0, cy = 0, cz = 0;
-  if (!all) {
-    if (mixed) {
-      cx = (int)(((uint64_t)(uint32_t)(ui[0] >> 32) * (uint64_t)nc) >> 32);
-      cy = (int)(((uint64_t)(uint32_t)(ui[1] >> 32) * (uint64_t)nc) >> 32);
-      cz = (int)(((uint64_t)(uint32_t)(ui[2] >> 32) * (uint64_t)nc) >> 32);
-    } else {
-      const double sc = (double)nc * R.invL;
-      cx = min(max((int)(xi[0] * sc), 0), nc - 1);
-      cy = min(max((int)(xi[1] * sc), 0), nc - 1);
-      cz = min(max((int)(xi[2] * sc), 0), nc - 1);
-    }
-  }
-  unsigned long long* h = hist + (int64_t)r * 3 * nbins;
-  auto visit = [&](int64_t j) {
-    if (j <= i) return;
-    double d[3];
+  if (act && i - R.off >= R.n) act = false;
+  if (act) {
+    const double rmax = dr * nbins, rmax2 = rmax * rmax;
+    const float rmax2f = (float)(rmax2 * (1.0 + 1e-4)) + 1e-6f;  // FP32 pre-test, widened
+    const float scf = R.fxs;
+    const int ti = typ[i];
+    double xi[3];
+    uint64_t ui[3];
     for (int c = 0; c < 3; ++c) {
+      if (mixed) ui[c] = pfx[c * ntot + i];
+      else xi[c] = c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z;
+    }
+    const uint4 qi = mixed ? pq[i] : make_uint4(0u, 0u, 0u, 0u);
+    const int nc = R.nc;
+    const int layers = nc > 0 ? (int)ceil((rmax + skin) * (1.0 + 1e-6) / (double)R.cellw) : 0;
+    const bool all = nc == 0 || 2 * layers + 1 > nc;
+    int cx = 0, cy = 0, cz = 0;
+    if (!all) {
       if (mixed) {
-        d[c] = (double)(int64_t)(ui[c] - pfx[c * ntot + j]) * (R.L * (1.0 / 18446744073709551616.0));
+        cx = (int)(((uint64_t)(uint32_t)(ui[0] >> 32) * (uint64_t)nc) >> 32);
+        cy = (int)(((uint64_t)(uint32_t)(ui[1] >> 32) * (uint64_t)nc) >> 32);
+        cz = (int)(((uint64_t)(uint32_t)(ui[2] >> 32) * (uint64_t)nc) >> 32);
       } else {
-        const double xj = c == 0 ? p4[j].x : c == 1 ? p4[j].y : p4[j].z;
-        double e = xi[c] - xj;
-        if (e > 0.5 * R.L) e -= R.L;
-        else if (e < -0.5 * R.L) e += R.L;
-        d[c] = e;
+        const double sc = (double)nc * R.invL;
+        cx = min(max((int)(xi[0] * sc), 0), nc - 1);
+        cy = min(max((int)(xi[1] * sc), 0), nc - 1);
+        cz = min(max((int)(xi[2] * sc), 0), nc - 1);
       }
     }
-    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < rmax2)) return;
-    const int k = (int)(sqrt(r2) / dr);
-    if (k >= nbins) return;
-    const int tj = typ[j];
-    if (ti == 0 && tj == 0) atomicAdd(&h[k], 2ull);
-    else if (ti == 1 && tj == 1) atomicAdd(&h[nbins + k], 2ull);
-    else atomicAdd(&h[2 * nbins + k], 1ull);
-  };
-  if (all) {
-    for (int64_t j = R.off; j < R.off + R.n; ++j) visit(j);
-  } else {
-    // cells are those of the last list build; every particle has moved less
-    // than half a skin since, so layers computed with rmax + skin cover all pairs
-    for (int oz = -layers; oz <= layers; ++oz)
-      for (int oy = -layers; oy <= layers; ++oy)
-        for (int ox = -layers; ox <= layers; ++ox) {
-          const int c = (((cz + oz + 8 * nc) % nc) * nc + (cy + oy + 8 * nc) % nc) * nc + (cx + ox + 8 * nc) % nc;
-          const int lo = cstart[R.cs0 + c], hi = cstart[R.cs0 + c + 1];
-          for (int j = lo; j < hi; ++j) visit(j);
+    unsigned long long* h = hist + (int64_t)r * 3 * nbins;
+    auto visit = [&](int64_t j) {
+      if (j <= i) return;
+      if (mixed) {
+        const uint4 qj = pq[j];
+        const float fx = (float)(int)(qi.x - qj.x) * scf, fy = (float)(int)(qi.y - qj.y) * scf,
+                    fz = (float)(int)(qi.z - qj.z) * scf;
+        if (!(fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < rmax2f)) return;
+      }
+      double d[3];
+      for (int c = 0; c < 3; ++c) {
+        if (mixed) {
+          d[c] = (double)(int64_t)(ui[c] - pfx[c * ntot + j]) * (R.L * (1.0 / 18446744073709551616.0));
+        } else {
+          const double xj = c == 0 ? p4[j].x : c == 1 ? p4[j].y : p4[j].z;
+          double e = xi[c] - xj;
+          if (e > 0.5 * R.L) e -= R.L;
+          else if (e < -0.5 * R.L) e += R.L;
+          d[c] = e;
         }
+      }
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 < rmax2)) return;
+      const int k = (int)(sqrt(r2) / dr);
+      if (k >= nbins) return;
+      const int tj = typ[j];
+      const int slot = (ti == 0 && tj == 0) ? k : ((ti == 1 && tj == 1) ? nbins + k : 2 * nbins + k);
+      const unsigned w = (ti == tj) ? 2u : 1u;
+      if (priv) atomicAdd(&sh_h[slot], w);
+      else atomicAdd(&h[slot], (unsigned long long)w);
+    };
+    if (all) {
+      for (int64_t j = R.off; j < R.off + R.n; ++j) visit(j);
+    } else {
+      // cells are those of the last list build; every particle has moved less
+      // than half a skin since, so layers computed with rmax + skin cover all pairs
+      for (int oz = -layers; oz <= layers; ++oz)
+        for (int oy = -layers; oy <= layers; ++oy)
+          for (int ox = -layers; ox <= layers; ++ox) {
+            const int c = (((cz + oz + 8 * nc) % nc) * nc + (cy + oy + 8 * nc) % nc) * nc + (cx + ox + 8 * nc) % nc;
+            const int lo = cstart[R.cs0 + c], hi = cstart[R.cs0 + c + 1];
+            for (int j = lo; j < hi; ++j) visit(j);
+          }
+    }
+  }
+  if (priv) {
+    __syncthreads();
+    unsigned long long* h = hist + (int64_t)sh_rep * 3 * nbins;
+    for (int t = threadIdx.x; t < 3 * nbins; t += blockDim.x)
+      if (sh_h[t]) atomicAdd(&h[t], (unsigned long long)sh_h[t]);
   }
 }
 
