@@ -359,6 +359,79 @@ def test_sampled_forces_one_million():
     assert err.max() <= TOL_F["mixed"], err.max()
 
 
+# Launch configurations the benchmark's autotuner settled on for each workload
+# (lanes per particle, CTA size, force-list skin, outer-list skin); the lists
+# are built and pruned by the timed-style launches before the forces are read.
+BENCH_LAUNCH = {
+    "ka32k": (4, 512, 0.3, 1.2),
+    "ka1m": (1, 512, 0.4, 0.4),
+    "ka8m": (1, 512, 0.4, 0.4),
+    "ensemble": (4, 256, 0.4, 0.4),
+}
+
+
+def sampled_force_errors(f, p, types, L, idx):
+    """|dF_i| / F_rms for the sampled particles, against O(N) oracle sums."""
+    t32 = types.astype(np.int32)
+    ref = np.array([oracle.force_on(p, t32, ka_params(), L, i)[0] for i in idx])
+    frms = np.sqrt(np.mean(np.sum(f * f, axis=1)))
+    return np.linalg.norm(f[idx] - ref, axis=1) / frms, frms
+
+
+@pytest.mark.parametrize("name,n,prec,nsamp", [
+    ("ka32k", 32000, "mixed", 300), ("ka32k", 32000, "fp64", 300),
+    ("ka1m", 1_000_000, "mixed", 200), ("ka8m", 8_000_000, "mixed", 48)])
+def test_sampled_forces_full_size_in_bench_launch(name, n, prec, nsamp):
+    """Full-size systems in the benchmark's launch configuration: a bath stage, then NVE launches
+    of 100 steps that rebuild (and, for two lists, prune) the lists, then sampled forces against
+    O(N) oracle sums, and the sum of all forces (zero by Newton's third law) against F_rms."""
+    L = wl.box_length(n)
+    types = wl.ka_types(n, 90 + len(name))
+    tpa, bs, skin, skin_out = BENCH_LAUNCH[name]
+    with make_system(n, L, types, prec) as s:
+        s.set_tuning(threads_per_atom=tpa, block_size=bs, skin=skin, skin_outer=skin_out)
+        s.init_lattice(2.0, 0.05, 90)
+        s.step_nvt(0.005, 60, 0.8, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5)
+        s.step_nve(0.005, 100)
+        s.step_nve(0.005, 100)
+        info = s.info()
+        f, pe, _ = s.forces()
+        p, _, _ = s.get_state()
+    assert info["rebuilds"] >= 2
+    if skin_out > skin:
+        assert info["prunes"] >= info["rebuilds"]
+    idx = np.random.default_rng(n).choice(n, size=nsamp, replace=False)
+    err, frms = sampled_force_errors(f, p, types, L, idx)
+    assert err.max() <= TOL_F[prec], err.max()
+    assert np.linalg.norm(f.sum(axis=0)) <= TOL_F[prec] * frms * np.sqrt(n)
+    assert np.isfinite(pe).all() and np.all((p >= 0) & (p < L))
+
+
+def test_sampled_forces_ensemble_in_bench_launch():
+    """The 512-replica mix (N in {250, ..., 8000}, about 1.3 million particles) in the benchmark's
+    launch configuration, after a Nose-Hoover stage at each replica's own temperature: one sampled
+    particle in every fourth replica against the O(N) oracle sum over its own box."""
+    spec = wl.ensemble(512, 4)
+    tpa, bs, skin, skin_out = BENCH_LAUNCH["ensemble"]
+    types = np.concatenate(spec.types)
+    with kamd.System(spec.n, spec.L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, 0.3, "mixed") as s:
+        s.set_tuning(threads_per_atom=tpa, block_size=bs, skin=skin, skin_outer=skin_out)
+        s.init_lattice(2.0, 0.05, 4)
+        s.step_nvt(0.005, 100, spec.T, kind=kamd.MD_NVT_NOSE_HOOVER, param=0.5)
+        f, pe, _ = s.forces()
+        p, _, _ = s.get_state()
+    assert pe.shape[0] == 512 and np.isfinite(pe).all()
+    off = np.concatenate([[0], np.cumsum(spec.n)])
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    for r in range(0, 512, 4):
+        a, b = off[r], off[r + 1]
+        i = int(rng.integers(0, b - a))
+        err, _ = sampled_force_errors(f[a:b], p[a:b], spec.types[r], spec.L[r], [i])
+        worst = max(worst, float(err[0]))
+    assert worst <= TOL_F["mixed"], worst
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_rdf_and_msd_match_oracle(prec):
     pos, vel, types, L = melted(1000, 91, nsteps=100)
