@@ -358,7 +358,9 @@ __device__ __forceinline__ void pair_mix(const Shared& sh, const uint4& pi, cons
 
 // Walk one lane's column of the list: each quad of indices is one 16-byte
 // load, issued one quad ahead of the gathers it feeds, so list and position
-// latencies overlap.
+// latencies overlap. List words are read once per pass, so they are loaded
+// with the evict-first (streaming) policy: once the list outgrows L2 it would
+// otherwise push out the gather copy that every pass re-reads.
 template <bool ENERGY>
 __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __restrict__ pq, const int* lp, int gsz,
                                              int cnt, int4 jq, const uint4& pi, int tb, float sc, float& fx,
@@ -368,7 +370,7 @@ __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __re
   int q = 0;
   for (; q + 4 <= cnt; q += 4) {
     const uint4 p0 = pq[jq.x], p1 = pq[jq.y], p2 = pq[jq.z], p3 = pq[jq.w];
-    if (q + 4 < cnt) jq = *reinterpret_cast<const int4*>(lp + (int64_t)((q + 4) >> 2) * qstride);
+    if (q + 4 < cnt) jq = __ldcs(reinterpret_cast<const int4*>(lp + (int64_t)((q + 4) >> 2) * qstride));
     pair_mix<ENERGY>(sh, pi, p0, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p1, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p2, tb, sc, fx, fy, fz, pe, vir);
@@ -423,7 +425,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
       // the first quad of list indices does not depend on the replica either
       // (slots past a replica's end have empty lists)
       int4 jq0 = make_int4(0, 0, 0, 0);
-      if (cnt0 > 0) jq0 = *reinterpret_cast<const int4*>(lp);
+      if (cnt0 > 0) jq0 = __ldcs(reinterpret_cast<const int4*>(lp));
       const RepDev* R = &p.reps[p.tile_rep[tile]];
       const bool act = (tile - R->tile0) * 32 + a < R->n;
       const int cnt = act ? cnt0 : 0;
@@ -490,7 +492,7 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
         const int tb = (int)pi.w * p.ntypes;
         const double L = R->L, hL = 0.5 * R->L;
         for (int q = 0; q < cnt; ++q) {
-          const int j = lp[list_at(0, q, gsz)];
+          const int j = __ldcs(lp + list_at(0, q, gsz));
           const double4_32a pj = p4[j];
           double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
@@ -621,14 +623,14 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
       // a quad ahead, and four position gathers in flight together
       const int64_t qstride = 4 * (int64_t)gsz;
       int4 jq = make_int4(0, 0, 0, 0);
-      if (cnt > 0) jq = *reinterpret_cast<const int4*>(lo);
+      if (cnt > 0) jq = __ldcs(reinterpret_cast<const int4*>(lo));
       for (int q = 0; q < cnt; q += 4) {
         const int m = min(4, cnt - q);
         const int j[4] = {jq.x, jq.y, jq.z, jq.w};
         uint4 pj[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) pj[u] = pq[u < m ? j[u] : j[0]];
-        if (q + 4 < cnt) jq = *reinterpret_cast<const int4*>(lo + (int64_t)((q + 4) >> 2) * qstride);
+        if (q + 4 < cnt) jq = __ldcs(reinterpret_cast<const int4*>(lo + (int64_t)((q + 4) >> 2) * qstride));
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float dx = (float)(int)(pi.x - pj[u].x) * sc;
@@ -645,7 +647,7 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
       const int tb = (int)pi.w * p.ntypes;
       const double L = R.L, hL = 0.5 * R.L;
       for (int q = 0; q < cnt; ++q) {
-        const int j = lo[list_at(0, q, gsz)];
+        const int j = __ldcs(lo + list_at(0, q, gsz));
         const double4_32a pj = p4[j];
         double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         if (dx > hL) dx -= L; else if (dx < -hL) dx += L;
