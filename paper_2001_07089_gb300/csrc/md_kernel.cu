@@ -357,20 +357,24 @@ __device__ __forceinline__ void pair_mix(const Shared& sh, const uint4& pi, cons
 }
 
 // Walk one lane's column of the list: each quad of indices is one 16-byte
-// load, issued one quad ahead of the gathers it feeds, so list and position
-// latencies overlap. List words are read once per pass, so they are loaded
-// with the evict-first (streaming) policy: once the list outgrows L2 it would
-// otherwise push out the gather copy that every pass re-reads.
+// load, issued two quads ahead of the gathers it feeds, so that a list read
+// from HBM has two rounds of pair terms to arrive. List words are read once
+// per pass, so they are loaded with the evict-first (streaming) policy: once
+// the list outgrows L2 it would otherwise push out the gather copy that every
+// pass re-reads.
 template <bool ENERGY>
 __device__ __forceinline__ void lane_sum_mix(const Shared& sh, const uint4* __restrict__ pq, const int* lp, int gsz,
                                              int cnt, int4 jq, const uint4& pi, int tb, float sc, float& fx,
                                              float& fy, float& fz, float& pe, float& vir) {
-  // jq: the column's first quad of indices, loaded by the caller
+  // jq: the column's first quad of indices, loaded by the caller; jn: the next
   const int64_t qstride = 4 * (int64_t)gsz;  // ints between consecutive quads of one column
+  int4 jn = make_int4(0, 0, 0, 0);
+  if (cnt > 4) jn = __ldcs(reinterpret_cast<const int4*>(lp + qstride));
   int q = 0;
   for (; q + 4 <= cnt; q += 4) {
     const uint4 p0 = pq[jq.x], p1 = pq[jq.y], p2 = pq[jq.z], p3 = pq[jq.w];
-    if (q + 4 < cnt) jq = __ldcs(reinterpret_cast<const int4*>(lp + (int64_t)((q + 4) >> 2) * qstride));
+    jq = jn;
+    if (q + 8 < cnt) jn = __ldcs(reinterpret_cast<const int4*>(lp + (int64_t)((q + 8) >> 2) * qstride));
     pair_mix<ENERGY>(sh, pi, p0, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p1, tb, sc, fx, fy, fz, pe, vir);
     pair_mix<ENERGY>(sh, pi, p2, tb, sc, fx, fy, fz, pe, vir);
