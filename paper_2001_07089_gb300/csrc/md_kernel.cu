@@ -597,12 +597,15 @@ __device__ void prune_phase(const KParams& p, Shared& sh, int cur, int64_t epoch
   const int gsz = 32 * T;
   const int lane = threadIdx.x & 31;
   const int nunits = p.ntiles * T;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAnd(&p.ctl->pending, ~MD_FLAG_PRUNE);
     p.ctl->prunes += 1;
   }
-  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nwarps) {
+  // the force phase's SM-local layout: neighbouring tiles, whose gathers
+  // overlap, are pruned on one SM and share its L1
+  int64_t ub, ue, us;
+  sm_share(sh, nunits, (int)(blockDim.x >> 5), (int)(threadIdx.x >> 5), &ub, &ue, &us);
+  for (int u = (int)ub; u < ue; u += (int)us) {
     const int tile = u / T;
     const int w = u - tile * T;
     const int rr = w * 32 + lane;
