@@ -88,19 +88,27 @@ class Clocks:
         time.sleep(0.25)
         self.proc.terminate()
         self.proc.wait(timeout=5)
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9 and f[1].replace(".", "").isdigit():
-                rows.append(f)
+        with open(self.path) as f:
+            rec = parse_clock_samples(f)
         os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = np.array([float(r[1]) for r in rows])
-        smax = max(float(r[2]) for r in rows)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+        return rec
+
+
+def parse_clock_samples(lines):
+    """Median SM clock, maximum clock and every throttle reason seen, from nvidia-smi CSV rows
+    (index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap)."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) >= 9 and f[1].replace(".", "").isdigit():
+            rows.append(f)
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    sm = np.array([float(r[1]) for r in rows])
+    smax = max(float(r[2]) for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
 def max_over_ranks(x, dist, device="cpu"):
