@@ -217,6 +217,23 @@ md_status md_rdf(md_system* sys, double dr, int64_t nbins, double* g, int reset)
  */
 md_status md_msd(md_system* sys, double* msd_per_type, int reset_reference);
 
+/*
+ * md_msd_tw: waiting-time mean square displacement per type (Eq. (msdtw) and
+ * its per-type form in the problems of Sec. "Mean square displacement"),
+ * <|r_i(t_w + t) - r_i(t_w)|^2> over the particles of each type and over
+ * replicas, against one of MD_MSD_SLOTS reference slots, so that several
+ * waiting times t_w can be followed along one trajectory (ageing after a
+ * quench, Sec. "Simulation Run Sequence"). reset_reference = 1 first takes
+ * the current unwrapped positions as the slot's r(t_w) (t = 0). Slot 0 is the
+ * reference of md_msd; the others get their device buffer (24 bytes per
+ * particle) at their first reset. msd_per_type: host, ntypes doubles, or NULL
+ * (reset only). Errors: MD_ERR_INVALID_ARG for a slot outside
+ * [0, MD_MSD_SLOTS) or one that has no reference yet (slots other than 0 lose
+ * theirs at md_set_state / md_init_lattice).
+ */
+#define MD_MSD_SLOTS 8
+md_status md_msd_tw(md_system* sys, int slot, double* msd_per_type, int reset_reference);
+
 /* md_set_tuning / md_get_tuning: change or read the launch configuration. */
 md_status md_set_tuning(md_system* sys, const md_tuning* t);
 md_status md_get_tuning(const md_system* sys, md_tuning* t);

@@ -62,3 +62,56 @@ def rdf_time_average(system: "kamd.System", dr: float, nbins: int, every: int, c
         advance(every)
         g = system.rdf(dr, nbins, reset=(k == 0))
     return g
+
+
+def waiting_time_msd(system: "kamd.System", t_ws: list[int], n_md: int, advance, t0: float = 1.0,
+                     kmax: int = 60) -> dict:
+    """Per-type <|r(t_w + t) - r(t_w)|^2> (Eq. (msdtw)) for several waiting times along one trajectory.
+
+    t_ws are waiting times in steps counted from the call (each gets its own
+    reference slot, 1 .. MD_MSD_SLOTS - 1); t runs over the log grid of
+    `log_time_grid(n_md, t0, kmax)`. `advance(n)` moves the system n steps
+    (NVE for an equilibrium run, NVT after a quench). Returns
+    {t_w: (t_steps, msd[len(t_steps), ntypes])}.
+    """
+    t_ws = [int(t) for t in t_ws]
+    if len(set(t_ws)) != len(t_ws) or min(t_ws, default=0) < 0:
+        raise ValueError("waiting times must be distinct and >= 0")
+    if len(t_ws) > kamd.MD_MSD_SLOTS - 1:
+        raise ValueError(f"at most {kamd.MD_MSD_SLOTS - 1} waiting times")
+    grid = log_time_grid(n_md, t0, kmax)
+    slot = {tw: k + 1 for k, tw in enumerate(sorted(t_ws))}
+    # events at each step: references first (order 0), then measurements (order 1)
+    events = sorted([(tw, 0, tw, -1) for tw in t_ws] +
+                    [(tw + s, 1, tw, k) for tw in t_ws for k, s in enumerate(grid)])
+    out = {tw: (np.array(grid, dtype=np.int64), np.zeros((len(grid), system.ntypes))) for tw in t_ws}
+    done = 0
+    for step, kind, tw, k in events:
+        if step > done:
+            advance(step - done)
+            done = step
+        if kind == 0:
+            system.msd_tw(slot[tw], reset_reference=True)
+        else:
+            out[tw][1][k] = system.msd_tw(slot[tw])
+    return out
+
+
+def cooling_ladder(system: "kamd.System", temperatures, dt: float, n_bath: int, n_nve: int, n_prod: int,
+                   nstep_boltz: int = 50, seed: int = 0, log_every: int = 0, production=None) -> list:
+    """The cooling sequence of Sec. "Simulation Run Sequence", applied to every replica at once.
+
+    For each temperature in turn: the stochastic bath for n_bath steps, NVE for
+    n_nve steps, then the production run: `production(system, T)` if given
+    (it advances the system itself and its result is kept), else n_prod NVE
+    steps. Each stage starts from the configuration the previous one left.
+    Returns one dict per temperature with the stages' thermo logs.
+    """
+    stages = []
+    for k, T in enumerate(temperatures):
+        bath = system.step_nvt(dt, n_bath, T, kind=kamd.MD_NVT_RESAMPLE, param=nstep_boltz, seed=seed + k,
+                               log_every=log_every)
+        nve = system.step_nve(dt, n_nve, log_every=log_every)
+        prod = production(system, T) if production is not None else system.step_nve(dt, n_prod, log_every=log_every)
+        stages.append({"T": T, "bath": bath, "nve": nve, "production": prod})
+    return stages

@@ -84,7 +84,8 @@ struct md_system {
   double* d_part[2] = {nullptr, nullptr};
   uint8_t* d_typ_caller = nullptr;
   int32_t* d_rep_of_caller = nullptr;
-  double* d_msd_ref = nullptr;
+  double* d_msd_ref[MD_MSD_SLOTS] = {};  // unwrapped reference positions r(t_w), caller order; [0] always held
+  bool msd_valid[MD_MSD_SLOTS] = {};
   ThermoDev* d_thermo = nullptr;
   int64_t thermo_cap = 0;
   double* d_io = nullptr;  // caller-order staging (n_total*3 doubles)
@@ -921,11 +922,16 @@ md_status ensure_thermo(md_system* s, int64_t records) {
   return MD_OK;
 }
 
-md_status reset_msd_ref(md_system* s) {
+// Take the current unwrapped positions as the reference r(t_w) of one MSD
+// slot (Eq. (msdtw)); slots other than 0 get their buffer on first use.
+md_status reset_msd_ref(md_system* s, int slot = 0) {
+  if (!s->d_msd_ref[slot]) CKS(dalloc(s, &s->d_msd_ref[slot], 3 * (size_t)s->n_total));
   const int b = 256;
   k_unwrapped<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(s->mixed, s->ntot, s->d_reps, s->d_tile_rep, s->d_pfx,
-                                                           s->d_p4[s->ctl.cur], s->d_gid, s->d_img, s->d_msd_ref);
+                                                           s->d_p4[s->ctl.cur], s->d_gid, s->d_img,
+                                                           s->d_msd_ref[slot]);
   CK(cudaGetLastError());
+  s->msd_valid[slot] = true;
   return MD_OK;
 }
 
@@ -944,6 +950,7 @@ md_status after_new_state(md_system* s) {
   CKS(upload_reps(s));
   CKS(upload_ctl(s));
   s->have_state = true;
+  for (int k = 1; k < MD_MSD_SLOTS; ++k) s->msd_valid[k] = false;  // references of the old state
   CKS(reset_msd_ref(s));
   s->rdf_meas = 0;
   return MD_OK;
@@ -1153,7 +1160,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   AL(s->d_part[1], (size_t)s->ntiles * 8 * MD_NPART);
   AL(s->d_typ_caller, (size_t)ntotal);
   AL(s->d_rep_of_caller, (size_t)ntotal);
-  AL(s->d_msd_ref, 3 * (size_t)ntotal);
+  AL(s->d_msd_ref[0], 3 * (size_t)ntotal);
   AL(s->d_io, 6 * (size_t)ntotal);
   AL(s->d_io_i, 3 * (size_t)ntotal);
   AL(s->d_msd_part, (size_t)s->ntiles * MD_NPART);
@@ -1349,21 +1356,27 @@ md_status md_rdf(md_system* s, double dr, int64_t nbins, double* g, int reset) {
   return MD_OK;
 }
 
-md_status md_msd(md_system* s, double* msd_per_type, int reset_reference) {
+md_status md_msd_tw(md_system* s, int slot, double* msd_per_type, int reset_reference) {
   if (!s) return fail(nullptr, MD_ERR_INVALID_ARG, "NULL system");
   if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state");
+  if (slot < 0 || slot >= MD_MSD_SLOTS) return fail(s, MD_ERR_INVALID_ARG, "MSD slot out of range");
   CKS(download_ctl(s));
-  if (reset_reference) CKS(reset_msd_ref(s));
+  if (reset_reference) CKS(reset_msd_ref(s, slot));
+  if (!s->msd_valid[slot]) return fail(s, MD_ERR_INVALID_ARG, "MSD slot has no reference (reset it first)");
   const int b = 256;
   k_msd_tiles<<<blocks_for((int64_t)s->ntiles * 32, b), b, 0, s->stream>>>(
       s->mixed, s->ntiles, s->ntypes, s->ntot, s->d_reps, s->d_tile_rep, s->d_pfx, s->d_p4[s->ctl.cur], s->d_gid,
-      s->d_typ, s->d_img, s->d_msd_ref, s->d_msd_part);
+      s->d_typ, s->d_img, s->d_msd_ref[slot], s->d_msd_part);
   CK(cudaGetLastError());
   k_msd_final<<<1, 32, 0, s->stream>>>(s->ntiles, s->ntypes, s->d_msd_part, s->d_io);
   CK(cudaGetLastError());
   if (msd_per_type) CK(cudaMemcpyAsync(msd_per_type, s->d_io, 8 * s->ntypes, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return MD_OK;
+}
+
+md_status md_msd(md_system* s, double* msd_per_type, int reset_reference) {
+  return md_msd_tw(s, 0, msd_per_type, reset_reference);
 }
 
 md_status md_set_tuning(md_system* s, const md_tuning* t) {
@@ -1621,8 +1634,9 @@ void md_destroy(md_system* s) {
   dfree(s, s->d_timg);
   dfree(s, s->d_cellof); dfree(s, s->d_cell_rep); dfree(s, s->d_ccount); dfree(s, s->d_cstart); dfree(s, s->d_ccursor); dfree(s, s->d_chunk); dfree(s, s->d_cta_sm); dfree(s, s->d_grp); dfree(s, s->d_redmap); dfree(s, s->d_redrep); dfree(s, s->d_redpart); dfree(s, s->d_scat);
   dfree(s, s->d_nbr); dfree(s, s->d_nnb); dfree(s, s->d_part[0]); dfree(s, s->d_part[1]);
-  dfree(s, s->d_typ_caller); dfree(s, s->d_rep_of_caller); dfree(s, s->d_msd_ref); dfree(s, s->d_thermo); dfree(s, s->d_io);
+  dfree(s, s->d_typ_caller); dfree(s, s->d_rep_of_caller); dfree(s, s->d_thermo); dfree(s, s->d_io);
   dfree(s, s->d_io_i); dfree(s, s->d_rdf); dfree(s, s->d_msd_part); dfree(s, s->d_count);
+  for (int k = 0; k < MD_MSD_SLOTS; ++k) dfree(s, s->d_msd_ref[k]);
   delete s;
 }
 

@@ -22,6 +22,7 @@ MD_OK, MD_ERR_INVALID_ARG, MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_UNSTABLE = 0, 1, 2, 3
 MD_ERR_NLIST_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_NOT_SUPPORTED = 5, 6, 7
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 MD_NVT_NOSE_HOOVER, MD_NVT_RESAMPLE, MD_NVT_NOSE_HOOVER_EXACT = 0, 1, 2
+MD_MSD_SLOTS = 8
 
 STATUS_NAMES = {0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD_ERR_UNSTABLE",
                 5: "MD_ERR_NLIST_OVERFLOW", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NOT_SUPPORTED"}
@@ -31,7 +32,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
                          ("h_nh", np.float64), ("xi", np.float64)])
 
 EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
-            "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_set_tuning", "md_get_tuning", "md_autotune",
+            "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_msd_tw", "md_set_tuning", "md_get_tuning", "md_autotune",
             "md_autotune_skin",
             "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_forces_noalloc", "md_last_error",
             "md_destroy")
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = True):
             "md_step_nvt": [P, dbl, i64, P, c_int, dbl, u64, P, i64],
             "md_rdf": [P, dbl, i64, P, c_int],
             "md_msd": [P, P, c_int],
+            "md_msd_tw": [P, c_int, P, c_int],
             "md_set_tuning": [P, ctypes.POINTER(md_tuning)],
             "md_get_tuning": [P, ctypes.POINTER(md_tuning)],
             "md_autotune": [P, dbl, i64, ctypes.POINTER(md_tuning), ctypes.POINTER(dbl)],
@@ -200,6 +202,10 @@ def md_rdf(h, dr, nbins, g, reset):
 
 def md_msd(h, out, reset_reference):
     _check(load().md_msd(h, out.ctypes.data if out is not None else None, int(reset_reference)), h)
+
+
+def md_msd_tw(h, slot, out, reset_reference):
+    _check(load().md_msd_tw(h, int(slot), out.ctypes.data if out is not None else None, int(reset_reference)), h)
 
 
 def md_set_tuning(h, tpa, block, skin, skin_outer):
@@ -351,6 +357,12 @@ class System:
     def msd(self, reset_reference=False):
         out = np.zeros(self.ntypes)
         md_msd(self._h, out, 1 if reset_reference else 0)
+        return out
+
+    def msd_tw(self, slot, reset_reference=False):
+        """Per-type MSD against reference slot `slot` (Eq. (msdtw)); reset = take r(t_w) now."""
+        out = np.zeros(self.ntypes)
+        md_msd_tw(self._h, slot, out, 1 if reset_reference else 0)
         return out
 
     @property

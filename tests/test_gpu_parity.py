@@ -432,6 +432,108 @@ def test_sampled_forces_ensemble_in_bench_launch():
     assert worst <= TOL_F["mixed"], worst
 
 
+class _MsdAgainstOracle:
+    """Wraps a system for the waiting-time schedule: at each reset the caller-order positions and
+    images are read back and kept as r(t_w); at each measurement the oracle's Eq. (msdwithi) is
+    evaluated on the same read-back state against that reference."""
+
+    def __init__(self, s, types, L):
+        self.s, self.types, self.L = s, types, L
+        self.ntypes = s.ntypes
+        self.ref, self.pairs = {}, []
+
+    def msd_tw(self, slot, reset_reference=False):
+        out = self.s.msd_tw(slot, reset_reference)
+        p, _, img = self.s.get_state()
+        if reset_reference:
+            self.ref[slot] = p + self.L * img
+        else:
+            self.pairs.append((out, oracle.msd(p, img, self.ref[slot], self.types, 2, self.L)))
+        return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_waiting_time_msd_matches_oracle(prec):
+    """Eq. (msdtw) for t_w = 0, 10, 100 steps along one NVE trajectory (slots 1-3), every point
+    against the oracle on the read-back state; slot 0 (md_msd) keeps its own reference."""
+    from paper_2001_07089_gb300 import analysis
+    pos, vel, types, L = melted(1000, 95, nsteps=100)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        chk = _MsdAgainstOracle(s, types, L)
+        res = analysis.waiting_time_msd(chk, [0, 10, 100], 200, advance=lambda n: s.step_nve(0.005, n), kmax=12)
+        p, _, img = s.get_state()
+        m0 = s.msd()
+    assert len(chk.pairs) == 3 * len(res[0][0])
+    for got, ref in chk.pairs:
+        assert np.allclose(got, ref, rtol=1e-9 if prec == "fp64" else 1e-5, atol=1e-14)
+    assert np.allclose(m0, oracle.msd(p, img, pos, types, 2, L), rtol=1e-9 if prec == "fp64" else 1e-5)
+    for tw in (0, 10, 100):
+        assert res[tw][1][-1, 0] > 10 * res[tw][1][0, 0] > 0.0  # particles move away from r(t_w)
+
+
+def test_msd_slots_reject_bad_use():
+    pos, vel, types, L = melted(250, 96, nsteps=50)
+    with make_system(250, L, types, "mixed") as s:
+        s.set_state(pos, vel)
+        with pytest.raises(kamd.KamdError):
+            s.msd_tw(kamd.MD_MSD_SLOTS, reset_reference=True)
+        with pytest.raises(kamd.KamdError):
+            s.msd_tw(-1)
+        with pytest.raises(kamd.KamdError):
+            s.msd_tw(3)  # never reset
+        s.msd_tw(3, reset_reference=True)
+        s.step_nve(0.005, 20)
+        assert np.all(s.msd_tw(3) > 0)
+        s.set_state(pos, vel)  # a new state: slots other than 0 lose their reference
+        with pytest.raises(kamd.KamdError):
+            s.msd_tw(3)
+        assert np.all(s.msd_tw(0) == 0.0)
+
+
+def test_cooling_ladder_batch_matches_standalone_and_oracle():
+    """The cooling sequence (stochastic bath, NVE, production at each temperature) on a batch of
+    two replicas: every replica bitwise equal to its stand-alone ladder, T exactly at target after
+    each bath, and the FP64 stand-alone run against the oracle stage by stage."""
+    from paper_2001_07089_gb300 import analysis
+    temps, nb, dt = [2.0, 1.0, 0.6], 10, 0.005
+    ns = [250, 500]
+    cfg = [melted(n, 97 + k, nsteps=50) for k, n in enumerate(ns)]
+    Ls = [c[3] for c in cfg]
+    with kamd.System(ns, Ls, np.concatenate([c[2] for c in cfg]), wl.KA_EPS, wl.KA_SIG, wl.KA_RC, 1.0, 0.3,
+                     "fp64") as b:
+        b.set_state(np.concatenate([c[0] for c in cfg]), np.concatenate([c[1] for c in cfg]))
+        bl = analysis.cooling_ladder(b, temps, dt, 20, 20, 20, nstep_boltz=nb, seed=5, log_every=10)
+        bp, bv, _ = b.get_state()
+    off = 0
+    for k, n in enumerate(ns):
+        pos, vel, types, L = cfg[k]
+        with make_system(n, L, types, "fp64") as s:
+            s.set_state(pos, vel)
+            sl = analysis.cooling_ladder(s, temps, dt, 20, 20, 20, nstep_boltz=nb, seed=5, log_every=10)
+            p, v, _ = s.get_state()
+        assert np.array_equal(p, bp[off:off + n]) and np.array_equal(v, bv[off:off + n])
+        for st_b, st_s in zip(bl, sl):
+            assert abs(st_s["bath"]["T"][-1, 0] - st_s["T"]) < 1e-12
+            for key in ("bath", "nve", "production"):
+                assert np.array_equal(st_b[key]["etot_per_n"][:, k], st_s[key]["etot_per_n"][:, 0])
+        if k == 0:
+            step, img = 0, np.zeros((n, 3), np.int32)
+            x, u = pos, vel
+            for j, st in enumerate(sl):
+                r = oracle.run(x, u, types, ka_params(), L, dt, 20, kind=oracle.RESAMPLE, T_target=st["T"],
+                               nstep_boltz=nb, seed=5 + j, img=img, step0=step, log_every=10)
+                assert thermo_rel(st["bath"], r["thermo"], "etot_per_n", 4) <= 1e-10
+                r2 = oracle.run(r["pos"], r["vel"], types, ka_params(), L, dt, 20, img=r["img"], step0=step + 20,
+                                log_every=10)
+                assert thermo_rel(st["nve"], r2["thermo"], "etot_per_n", 4) <= 1e-10
+                r3 = oracle.run(r2["pos"], r2["vel"], types, ka_params(), L, dt, 20, img=r2["img"],
+                                step0=step + 40, log_every=10)
+                assert thermo_rel(st["production"], r3["thermo"], "etot_per_n", 4) <= 1e-10
+                x, u, img, step = r3["pos"], r3["vel"], r3["img"], step + 60
+        off += n
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_rdf_and_msd_match_oracle(prec):
     pos, vel, types, L = melted(1000, 91, nsteps=100)

@@ -390,3 +390,24 @@ def test_msd_free_flight_and_unwrapping():
     assert out["img"][0, 0] == -1 and out["img"][2, 2] == 0 and out["img"][3, 2] == 1
     still = oracle.msd(pos, np.zeros((4, 3), np.int32), pos, types, 2, L)
     assert np.all(still == 0.0)
+
+
+def test_waiting_time_msd_free_flight():
+    """Eq. (msdtw): with the reference taken at t_w (unwrapped positions then), free flight gives
+    <v^2> t^2 for every t_w, also when particles cross the boundary before or after t_w; t_w = 0
+    is Eq. (msd)."""
+    L = 40.0
+    pos = np.array([[1.0, 1.0, 1.0], [15.0, 15.0, 15.0], [30.0, 5.0, 20.0], [10.0, 32.0, 36.0]])
+    vel = np.array([[-2.0, 0.5, 0.0], [1.0, 1.0, -1.0], [0.0, 0.0, 3.0], [0.5, -1.5, 2.0]])
+    types = np.array([0, 0, 1, 1], dtype=np.int32)
+    v2 = np.sum(vel * vel, axis=1)
+    dt = 0.01
+    for tw in (0, 50, 120):
+        a = oracle.run(pos, vel, types, ka_params(), L, dt, tw, log_every=0) if tw else {
+            "pos": pos, "vel": vel, "img": np.zeros((4, 3), np.int32)}
+        ref = a["pos"] + L * a["img"]
+        b = oracle.run(a["pos"], a["vel"], types, ka_params(), L, dt, 100, img=a["img"], log_every=0)
+        msd = oracle.msd(b["pos"], b["img"], ref, types, 2, L)
+        t = 100 * dt
+        assert msd[0] == pytest.approx(v2[:2].mean() * t * t, rel=1e-12)
+        assert msd[1] == pytest.approx(v2[2:].mean() * t * t, rel=1e-12)
