@@ -8,7 +8,8 @@ device when any particle has moved more than skin/2; the autotuner may add an
 outer list that the force list is pruned from). Other lines: --workload ka1m
 (10^6 particles, Nose-Hoover at T = 0.5, with the cost of the g(r) and MSD
 calls reported separately), ka8m (8*10^6, quench 2.0 -> 0.45 then NVE, with
-the device footprint), ensemble (512 replicas in one launch).
+the device footprint), ensemble (512 replicas in one launch), ladder (the
+paper's cooling run sequence, 8 replicas of N = 1000 in one launch).
 
 One bench step = one persistent launch that advances the system 100 MD steps
 (force + velocity Verlet + reductions + every list rebuild the dynamics
@@ -154,6 +155,14 @@ WORKLOADS = {
                      desc="ensemble: 512 independent KA replicas in one persistent launch, N per replica uniform "
                           "over {250,500,1000,2000,4000,8000}, rho=1.2, per-replica Nose-Hoover at T uniform in "
                           "[0.45,2.0], dt=0.005; one bench step = 100 MD steps of every replica"),
+    "ladder": dict(kind="ladder", nrep=8, n=1000, seed=6, T0=5.0, timed="ladder",
+                   temps=[5.0, 4.0, 3.0, 2.0, 1.0, 0.8, 0.6, 0.55, 0.5, 0.475, 0.466],
+                   desc="ladder: the cooling run sequence on 8 independent KA replicas of N=1000 (rho=1.2, L=9.4104) "
+                        "in one launch: lattice+0.05 jitter, 200 steps of the stochastic bath at T=5.0 (untimed), "
+                        "then per temperature T=5.0, 4.0, 3.0, 2.0, 1.0, 0.8, 0.6, 0.55, 0.5, 0.475, 0.466 one "
+                        "bench step of the stochastic bath (redraw every 50 steps), one of NVE and one NVE "
+                        "production step, dt=0.005; one bench step = 100 MD steps of every replica; e2e = NVE "
+                        "launches of the same batch"),
 }
 
 
@@ -166,6 +175,13 @@ def setup_system(kamd, wl, prec, device, wk=None):
         types = wl.ka_types(n, wk["seed"])
         s = kamd.System(n, L, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
         T = np.array([wk["T"]])
+    elif wk["kind"] == "ladder":
+        n_per = [wk["n"]] * wk["nrep"]
+        L = wl.box_length(wk["n"])
+        types = np.concatenate([wl.ka_types(wk["n"], wk["seed"] * 100003 + r) for r in range(wk["nrep"])])
+        s = kamd.System(n_per, [L] * wk["nrep"], types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
+        n = wk["n"] * wk["nrep"]
+        T = np.full(wk["nrep"], wk["T0"])
     else:
         spec = wl.ensemble(wk["nrep"], wk["seed"])
         s = kamd.System(spec.n, spec.L, np.concatenate(spec.types), wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS,
@@ -176,7 +192,10 @@ def setup_system(kamd, wl, prec, device, wk=None):
     if "pre_nvt" in wk:  # a first bath stage before the quench to T
         T0, k0 = wk["pre_nvt"]
         s.step_nvt(wl.DT, k0, np.full_like(T, T0), kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
-    s.step_nvt(wl.DT, wk["setup_nvt"], T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
+    if wk["kind"] == "ladder":  # equilibrate at the top of the ladder with the stochastic bath
+        s.step_nvt(wl.DT, 200, T, kind=kamd.MD_NVT_RESAMPLE, param=50, seed=wk["seed"])
+    else:
+        s.step_nvt(wl.DT, wk["setup_nvt"], T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
     return s, n, T
 
 
@@ -362,6 +381,19 @@ def main():
     def stepper(sys_, T):
         if wk["timed"] == "nve":
             return lambda k, le: sys_.step_nve(wl.DT, k, log_every=le)
+        if wk["timed"] == "ladder":
+            # bench step j: stage j % 3 (bath, NVE, production) at temperature j // 3 of the ladder
+            state = {"j": 0}
+
+            def ladder_step(k, le):
+                j = state["j"]
+                state["j"] += 1
+                Tk = wk["temps"][(j // 3) % len(wk["temps"])]
+                if j % 3 == 0:
+                    return sys_.step_nvt(wl.DT, k, Tk, kind=kamd.MD_NVT_RESAMPLE, param=50, seed=wk["seed"] + j,
+                                         log_every=le)
+                return sys_.step_nve(wl.DT, k, log_every=le)
+            return ladder_step
         return lambda k, le: sys_.step_nvt(wl.DT, k, T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT,
                                            log_every=le)
 
@@ -398,7 +430,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(3, min(args.steps, 20))
-        e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, e2e_steps, None if wk["timed"] == "nve" else T)
+        e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, e2e_steps, None if wk["timed"] in ("nve", "ladder") else T)
         e2e = {"value": world * n_sys * CHUNK * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     s.close()
