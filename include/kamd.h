@@ -278,8 +278,8 @@ md_status md_selftest_barrier(md_system* sys, double timeout_s);
 
 /*
  * md_forces_noalloc: forces, shifted potential energy and virial of one
- * configuration, computed without allocating any memory. (The paper has no
- * counterpart: this is an interface for callers that cannot allocate.)
+ * configuration, computed without allocating any memory. The paper has no
+ * counterpart: this is an interface for callers that cannot allocate.
  *
  * Who needs it: code that enqueues work while a stream is being captured
  * into a CUDA graph (cudaMalloc is not allowed inside a capture), real-time
@@ -289,25 +289,31 @@ md_status md_selftest_barrier(md_system* sys, double timeout_s);
  *
  * All scratch lives in one static device array of 1.4 MiB that every GPU
  * which loads the library holds until the process exits. Hence the limits:
- * 2 <= n <= 131072 particles and at most 32768 cells (larger boxes use fewer,
- * larger cells); larger n is rejected with MD_ERR_INVALID_ARG and a message
- * in md_last_error(NULL).
+ * 2 <= n <= 131072 particles and at most 32 cells per box edge (larger boxes
+ * use larger cells); larger n is rejected with MD_ERR_INVALID_ARG and a
+ * message in md_last_error(NULL).
  *   pos     device, n*3 doubles (any real values; wrapped into [0, L))
- *   types   device, n uint8 in [0, ntypes)
+ *   types   device, n uint8 in [0, ntypes). A value >= ntypes is never used
+ *           as a table index: that particle's force, and the force of every
+ *           particle that meets it in the cell search, comes out NaN, and so
+ *           do pe and virial.
  *   eps, sigma, rc  host tables as in md_create (rc < L/2)
  *   f       device, n*3 doubles (output, caller order)
  *   pe, virial  device, one double each (outputs; may be NULL)
  *   stream  cudaStream_t for all work (NULL: legacy default stream)
- * Arithmetic is the FP64 path of md_forces (Eqs. (KAFix), (VshiftedKALJ),
- * minimum image of Sec. "Periodic boundary conditions") over a cell list of
+ * The arithmetic is that of md_forces on the FP64 path, over a cell list of
  * cell edge >= the largest cutoff; results are deterministic.
- * The call only enqueues work and returns. Its first call on a device (with
- * that device current) looks up the device address of the static array;
- * make that first call before any stream capture. Every call on a device
- * shares the one array, which keeps the previous call's contents (each call
- * clears what must start at zero): calls that overlap on the GPU -- on
- * different streams, or from different host threads -- race and give wrong
- * results; order them.
+ * The call only enqueues work and returns. The host-side name of the static
+ * array is not a device address, so every call made outside a stream capture
+ * looks up the array's device address in the current CUDA context; a call
+ * made while its stream is being captured uses the address found by the last
+ * uncaptured call in the same context. Hence: make one call in each context
+ * (and again after cudaDeviceReset) before capturing a stream; a captured
+ * call with no earlier one fails with MD_ERR_INVALID_ARG. Every call on a
+ * device shares the one array, which keeps the previous call's contents
+ * (each call clears what must start at zero): calls that overlap on the GPU
+ * -- on different streams, or from different host threads -- race and give
+ * wrong results; order them.
  */
 md_status md_forces_noalloc(int64_t n, const double* pos, const uint8_t* types, int ntypes, double L,
                             const double* eps, const double* sigma, const double* rc,

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "kamd.h"
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int64_t kMaxParticles = 131072;  // 2^17
 constexpr int kMaxCells = 32768;
+constexpr int kMaxCellsPerEdge = 32;  // kMaxCells = 32^3
 constexpr int kBlock = 256;
 constexpr int kMaxBlocks = (int)(kMaxParticles / kBlock);
 constexpr int kMaxTypes = 4;
@@ -167,9 +169,12 @@ __global__ void k_forces(Scratch s, const double* pos, const uint8_t* types, int
   if (i < n) {
     const double xi[3] = {wrap01(pos[3 * i], L), wrap01(pos[3 * i + 1], L), wrap01(pos[3 * i + 2], L)};
     const int ti = types[i];
+    // a type outside [0, ntypes) never indexes the tables: the particle's
+    // results (and those of particles that meet it) become NaN instead
+    bool bad = ti >= ntypes;
     const double hL = 0.5 * L;
     auto pair = [&](int64_t j) {
-      if (j == i) return;
+      if (j == i || bad) return;
       double d[3];
       for (int k = 0; k < 3; ++k) {
         double e = xi[k] - wrap01(pos[3 * j + k], L);
@@ -178,7 +183,12 @@ __global__ void k_forces(Scratch s, const double* pos, const uint8_t* types, int
         d[k] = e;
       }
       const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      const int t = ti * ntypes + types[j];
+      const int tj = types[j];
+      if (tj >= ntypes) {
+        bad = true;
+        return;
+      }
+      const int t = ti * ntypes + tj;
       if (r2 < tab.rc2[t]) {
         const double ir2 = 1.0 / r2;
         const double s2 = tab.sig2[t] * ir2;
@@ -204,6 +214,7 @@ __global__ void k_forces(Scratch s, const double* pos, const uint8_t* types, int
     } else {
       for (int64_t j = 0; j < n; ++j) pair(j);
     }
+    if (bad) fx = fy = fz = pe = vir = __longlong_as_double(0x7ff8000000000000ll);
     f[3 * i] = fx;
     f[3 * i + 1] = fy;
     f[3 * i + 2] = fz;
@@ -240,11 +251,72 @@ __global__ void k_forces(Scratch s, const double* pos, const uint8_t* types, int
   }
 }
 
-unsigned char* g_scratch_ptr[64] = {nullptr};
-
 md_status noalloc_fail(md_status st, const std::string& m) {
   kamd_set_global_error(m);
   return st;
+}
+
+// Device address of the static scratch array, per CUDA context. The host-side
+// name g_noalloc_scratch is a stand-in, not a device address, and the array
+// moves whenever the module is loaded again (a new context after
+// cudaDeviceReset, or another context on the same device). So the address is
+// looked up afresh on every call made outside a stream capture, and the
+// cached value of the current context is used only while a capture is open
+// (where the look-up itself is not allowed).
+typedef int (*CtxGetCurrentFn)(void**);
+
+struct ScratchSlot {
+  void* ctx;
+  unsigned char* ptr;
+};
+constexpr int kSlots = 64;
+ScratchSlot g_slots[kSlots];
+int g_nslots = 0;
+std::mutex g_slots_mu;
+
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
+md_status scratch_address(cudaStream_t st, unsigned char** out) {
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return noalloc_fail(MD_ERR_CUDA, "md_forces_noalloc: cuCtxGetCurrent is not available");
+  // the capture query also sets up the runtime's context on this thread if
+  // nothing else has yet
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return noalloc_fail(MD_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  void* ctx = nullptr;
+  if (get(&ctx) != 0 || !ctx) return noalloc_fail(MD_ERR_CUDA, "md_forces_noalloc: no current CUDA context");
+  std::lock_guard<std::mutex> lock(g_slots_mu);
+  int k = 0;
+  while (k < g_nslots && g_slots[k].ctx != ctx) ++k;
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (k == g_nslots)
+      return noalloc_fail(MD_ERR_INVALID_ARG,
+                          "md_forces_noalloc: make one call in this CUDA context before capturing a stream");
+    *out = g_slots[k].ptr;
+    return MD_OK;
+  }
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return noalloc_fail(MD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  if (k == g_nslots) {
+    if (g_nslots == kSlots) k = 0;  // many contexts: reuse the oldest slot
+    else ++g_nslots;
+  }
+  g_slots[k] = ScratchSlot{ctx, static_cast<unsigned char*>(ptr)};
+  *out = g_slots[k].ptr;
+  return MD_OK;
 }
 
 }  // namespace
@@ -275,25 +347,17 @@ extern "C" md_status md_forces_noalloc(int64_t n, const double* pos, const uint8
       tab.vsh[t] = 4.0 * eps[t] * (sr6 * sr6 - sr6);
       rcmax = std::max(rcmax, rc[t]);
     }
-  int nc = (int)std::floor(L / rcmax);
+  // cells of edge >= the largest cutoff, at most kMaxCellsPerEdge per edge
+  // (clamped in double, so any finite L is safe); fewer than 3: all pairs
+  int nc = (int)std::min(std::floor(L / rcmax), (double)kMaxCellsPerEdge);
   if (nc < 3) nc = 1;
-  while ((int64_t)nc * nc * nc > kMaxCells) --nc;
   const int ncells = nc * nc * nc;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(MD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return noalloc_fail(MD_ERR_NOT_SUPPORTED, "md_forces_noalloc: device index >= 64");
-  if (!g_scratch_ptr[dev]) {
-    // first call on this device: resolve the device address of the static
-    // scratch array (the host-side symbol is not a device address)
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return noalloc_fail(MD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(ptr);
-  }
-  const Scratch s = carve(g_scratch_ptr[dev]);
   cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  const md_status as = scratch_address(st, &base);
+  if (as != MD_OK) return as;
+  const Scratch s = carve(base);
+  cudaError_t e;
   const int nb = (int)((n + kBlock - 1) / kBlock);
   k_clear<<<std::max(1, std::min(64, (ncells + kBlock - 1) / kBlock)), kBlock, 0, st>>>(s, ncells);
   k_bin<<<nb, kBlock, 0, st>>>(s, pos, n, nc, L);
