@@ -5,11 +5,14 @@ Workload (the 32k configuration): lattice + 0.05 jitter start at T = 2.0,
 2000 Nose-Hoover steps to T = 0.8 (set-up, untimed), then NVE at dt = 0.005
 with a cell + Verlet list whose force-list skin is 0.3 (rebuilt on the
 device when any particle has moved more than skin/2; the autotuner may add an
-outer list that the force list is pruned from). Other lines: --workload ka1m
-(10^6 particles, Nose-Hoover at T = 0.5, with the cost of the g(r) and MSD
-calls reported separately), ka8m (8*10^6, quench 2.0 -> 0.45 then NVE, with
-the device footprint), ensemble (512 replicas in one launch), ladder (the
-paper's cooling run sequence, 8 replicas of N = 1000 in one launch).
+outer list that the force list is pruned from). Other lines: --workload ka1k
+(N = 1000 on the all-FP64 path, NVE from the lattice start at T = 2.0),
+ka1m (10^6 particles, Nose-Hoover at T = 0.5, with the cost of the g(r) and
+MSD calls reported separately), ka8m (8*10^6, quench 2.0 -> 0.45 then NVE,
+with the device footprint), ensemble (512 replicas in one launch; with N
+ranks the replicas are split over them by a greedy N-balanced partition),
+ladder (the paper's cooling run sequence, 8 replicas of N = 1000 in one
+launch).
 
 One bench step = one persistent launch that advances the system 100 MD steps
 (force + velocity Verlet + reductions + every list rebuild the dynamics
@@ -17,16 +20,23 @@ triggers), i.e. one md_step_nve(dt, 100) call. --steps K timed steps follow
 --warmup W untimed ones; the default K = 100 covers the configuration's
 10 000 NVE steps. L2 is flushed (a 256 MB write) between timed steps.
 
-value     = atom-steps/s of the mixed-precision path, device-timed (CUDA
-            events on the system's stream), inputs resident in HBM.
+value     = atom-steps/s of the mixed-precision path (ka1k: FP64),
+            device-timed (CUDA events on the system's stream), inputs
+            resident in HBM; with N ranks, all ranks' atoms over the slowest
+            rank's time.
 e2e       = the same metric through the public C ABI with host buffers:
             md_set_state(host) + md_step_nve(100, thermo log to host) +
             md_get_state(host) per step.
-fp64      = the all-FP64 GPU path on the same protocol, with its drift.
+drift     = slope of E_tot/N against t over the timed NVE window, with a
+            moving-block bootstrap error; fp64 = the all-FP64 GPU path on the
+            same protocol and the same window, with its drift;
+            drift_equal_or_better = the metric's condition (mixed drift not
+            larger than the FP64 drift beyond two combined error bars).
 roofline  = FP32 issue bound ("alu") of the persistent kernel: algorithmic
             FLOPs per launch / launch time against 2*128*SMs*f_max.
-cpu_baseline = the FP64 oracle (plain C, all pairs, one core) on a bounded
-            sample (a few MD steps of the same system).
+cpu_baseline = the FP64 oracle (plain C, all pairs) on a bounded sample (a
+            few MD steps of the same system) on every host core, with the
+            one-thread rate beside it.
 """
 from __future__ import annotations
 
@@ -122,23 +132,69 @@ def max_over_ranks(x, dist, device="cpu"):
     return float(t.item())
 
 
+def sum_over_ranks(x, dist, device="cuda"):
+    """Sum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def whole_job_rate(world, n_per_rank, md_steps, max_seconds):
     """Atom-steps/s of the whole job: every rank advances its own replica."""
     return world * n_per_rank * md_steps / max_seconds
 
 
 def drift_per_tau(log, dt):
-    """Least-squares slope of E_tot/N against time (energy per particle per tau)."""
-    e = log["etot_per_n"][:, 0]
-    t = log["step"][:, 0] * dt
-    if len(e) < 3:
-        return None, None
-    A = np.vstack([t, np.ones_like(t)]).T
-    coef, *_ = np.linalg.lstsq(A, e, rcond=None)
-    return float(coef[0]), float(np.std(e - A @ coef))
+    """Least-squares slope of E_tot/N against time (energy per particle per tau) and the RMS
+    fluctuation about it."""
+    d = drift_stats(log, dt)
+    return d["slope"], d["rms"]
+
+
+def drift_stats(log, dt):
+    """Drift of E_tot/N (first replica) over the logged window: slope, moving-block bootstrap error
+    of the slope, RMS fluctuation about the fit, window length in steps."""
+    from paper_2001_07089_gb300 import analysis
+    e = np.asarray(log["etot_per_n"][:, 0], dtype=np.float64)
+    st = np.asarray(log["step"][:, 0], dtype=np.float64)
+    if len(e) < 4:
+        return {"slope": None, "err": None, "rms": None, "window_steps": 0}
+    d = analysis.drift_fit(st * dt, e)
+    return {"slope": d["slope"], "err": d["err"], "rms": d["rms"], "window_steps": int(st[-1] - st[0])}
+
+
+def drift_equal_or_better(mixed, fp64, k=2.0):
+    """The metric's condition: the mixed path's drift magnitude is not larger than the FP64 path's
+    beyond k combined error bars. None when either drift is missing."""
+    if not mixed or not fp64 or mixed.get("slope") is None or fp64.get("slope") is None:
+        return None
+    sig = float(np.hypot(mixed["err"], fp64["err"]))
+    return bool(abs(mixed["slope"]) <= abs(fp64["slope"]) + k * sig)
+
+
+def partition_replicas(n_per, world):
+    """Greedy N-balanced split of independent replicas over `world` ranks: largest replica first,
+    each to the rank with the least load so far (lowest rank on ties). Returns one sorted index
+    list per rank."""
+    n_per = [int(x) for x in n_per]
+    order = sorted(range(len(n_per)), key=lambda r: (-n_per[r], r))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for r in order:
+        k = min(range(world), key=lambda q: (load[q], q))
+        parts[k].append(r)
+        load[k] += n_per[r]
+    return [sorted(p) for p in parts]
 
 
 WORKLOADS = {
+    "ka1k": dict(kind="single", n=1000, seed=1, T0=2.0, T=None, setup_nvt=0, timed="nve", skin=0.3, prec="fp64",
+                 desc="ka1k: Kob-Andersen 80:20, N=1000, rho=1.2, L=9.4104, 10^3 lattice+0.05 jitter, Maxwell-"
+                      "Boltzmann T=2.0, NVE dt=0.005 on the all-FP64 path (no bath stage); force-list skin 0.3; "
+                      "one bench step = 100 MD steps (--steps 10 = the configuration's 1000 steps)"),
     "ka32k": dict(kind="single", n=32000, seed=2, T0=2.0, T=0.8, setup_nvt=2000, timed="nve", skin=0.3,
                   desc="ka32k: Kob-Andersen 80:20, N=32000, rho=1.2, L=29.876, lattice+0.05 jitter at T=2.0, "
                        "2000 Nose-Hoover steps to T=0.8 (untimed), then NVE dt=0.005; cell + Verlet list, force-list skin 0.3 (any outer list autotuned) "
@@ -166,8 +222,9 @@ WORKLOADS = {
 }
 
 
-def setup_system(kamd, wl, prec, device, wk=None):
-    """Build, start and equilibrate the workload's system; returns (system, n_total, T_target)."""
+def setup_system(kamd, wl, prec, device, wk=None, subset=None):
+    """Build, start and equilibrate the workload's system; returns (system, n_total, T_target).
+    subset: replica indices of the ensemble this rank runs (all when None)."""
     wk = wk or WORKLOADS["ka32k"]
     if wk["kind"] == "single":
         n = wk["n"]
@@ -184,17 +241,18 @@ def setup_system(kamd, wl, prec, device, wk=None):
         T = np.full(wk["nrep"], wk["T0"])
     else:
         spec = wl.ensemble(wk["nrep"], wk["seed"])
-        s = kamd.System(spec.n, spec.L, np.concatenate(spec.types), wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS,
-                        wl.SKIN, prec)
-        n = spec.total
-        T = spec.T
+        idx = list(range(len(spec.n))) if subset is None else list(subset)
+        s = kamd.System(spec.n[idx], spec.L[idx], np.concatenate([spec.types[r] for r in idx]), wl.KA_EPS, wl.KA_SIG,
+                        wl.KA_RC, wl.KA_MASS, wl.SKIN, prec)
+        n = int(spec.n[idx].sum())
+        T = spec.T[idx]
     s.init_lattice(wk["T0"], 0.05, wk["seed"])
     if "pre_nvt" in wk:  # a first bath stage before the quench to T
         T0, k0 = wk["pre_nvt"]
         s.step_nvt(wl.DT, k0, np.full_like(T, T0), kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
     if wk["kind"] == "ladder":  # equilibrate at the top of the ladder with the stochastic bath
         s.step_nvt(wl.DT, 200, T, kind=kamd.MD_NVT_RESAMPLE, param=50, seed=wk["seed"])
-    else:
+    elif wk["setup_nvt"] > 0:
         s.step_nvt(wl.DT, wk["setup_nvt"], T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT)
     return s, n, T
 
@@ -293,8 +351,18 @@ def profiled_traffic(workload, tuning):
         return None
 
 
-def cpu_baseline(wl, seconds_target=15.0):
-    """The oracle as it stands (one core, all pairs) on a few MD steps of the same system."""
+def host_threads():
+    """Host cores the oracle may use (its threaded force sum), at most 64."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(64, n))
+
+
+def cpu_baseline(wl, seconds_target=12.0):
+    """The oracle as it stands (all-pairs FP64) on a few MD steps of the same N = 32 000 system: on
+    one thread (the plain oracle) and on every host core (its threaded force sum)."""
     import oracle
     L = wl.box_length(N)
     types = wl.ka_types(N, SEED).astype(np.int32)
@@ -303,15 +371,28 @@ def cpu_baseline(wl, seconds_target=15.0):
     t0 = time.perf_counter()
     f, _, _ = oracle.forces(pos, types, params, L)
     t_force = time.perf_counter() - t0
-    nsteps = max(1, min(10, int(seconds_target / max(t_force, 1e-3)) - 1))
+    n1 = max(1, min(10, int(0.5 * seconds_target / max(t_force, 1e-3)) - 1))
     t0 = time.perf_counter()
-    oracle.run(pos, vel, types, params, L, wl.DT, nsteps, forces_in=f, log_every=0)
-    el = time.perf_counter() - t0
-    return {"value": N * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} velocity-Verlet steps of the N=32000 system (all-pairs FP64 C oracle, 1 thread)"}
+    oracle.run(pos, vel, types, params, L, wl.DT, n1, forces_in=f, log_every=0)
+    v1 = N * n1 / (time.perf_counter() - t0)
+    cores = host_threads()
+    nall = max(1, min(100, int(0.5 * seconds_target * v1 * cores * 0.7 / N)))
+    oracle.set_threads(cores)
+    try:
+        t0 = time.perf_counter()
+        oracle.run(pos, vel, types, params, L, wl.DT, nall, forces_in=f, log_every=0)
+        vall = N * nall / (time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(1)
+    return {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nall} velocity-Verlet steps of the N=32000 system, all-pairs FP64 C oracle on {cores} "
+                      f"threads (per-thread force arrays added in thread order); on 1 thread: {n1} steps",
+            "value_1_thread": v1}
 
 
 def reference_arm(args, rank, world):
+    """The tier's reference arm: the oracle as it stands (all-pairs FP64 C, its threaded force sum on
+    every host core), one bench step = one MD step of the N = 32 000 system. Rank 0 only."""
     import torch.distributed as dist  # noqa: F401
     from paper_2001_07089_gb300 import workloads as wl
     if rank != 0:
@@ -321,14 +402,19 @@ def reference_arm(args, rank, world):
     types = wl.ka_types(N, SEED).astype(np.int32)
     params = oracle.Params(wl.KA_EPS, wl.KA_SIG, wl.KA_RC, wl.KA_MASS)
     pos, vel = oracle.init_lattice(N, L, T_START, SEED)
-    f, _, _ = oracle.forces(pos, types, params, L)
-    st = {"pos": pos, "vel": vel, "forces": f}
-    for _ in range(args.warmup):
-        st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
-    el = time.perf_counter() - t0
+    cores = host_threads()
+    oracle.set_threads(cores)
+    try:
+        f, _, _ = oracle.forces_threads(pos, types, params, L, cores)
+        st = {"pos": pos, "vel": vel, "forces": f}
+        for _ in range(args.warmup):
+            st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = oracle.run(st["pos"], st["vel"], types, params, L, wl.DT, 1, forces_in=st["forces"], log_every=0)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
     v = N * args.steps / el
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -336,8 +422,9 @@ def reference_arm(args, rank, world):
                       "data": "synthetic",
                       "config": {"workload": "ka32k: KA 80:20 N=32000 rho=1.2, NVE dt=0.005; one bench step = one "
                                              "oracle MD step (all pairs)"},
-                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                       "sample": f"{args.steps} all-pairs velocity-Verlet steps of N=32000, 1 thread"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": f"{args.steps} all-pairs velocity-Verlet steps of N=32000 on "
+                                                 f"{cores} threads"},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -354,7 +441,7 @@ def main():
                     help="fixed tuning 'threads_per_atom,block_size,skin,skin_outer' instead of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None,
-                    help="timed bench steps of the all-FP64 arm (default: min(steps, 20) for ka32k, 0 otherwise)")
+                    help="timed bench steps of the all-FP64 arm (default: --steps for ka32k, 0 otherwise)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.warmup < 3:
@@ -397,8 +484,14 @@ def main():
         return lambda k, le: sys_.step_nvt(wl.DT, k, T, kind=kamd.MD_NVT_NOSE_HOOVER, param=100 * wl.DT,
                                            log_every=le)
 
-    # ---- mixed-precision path (the measured value); every rank runs its own system
-    s, n_sys, T = setup_system(kamd, wl, "mixed", dev, wk)
+    # ---- the measured path (mixed precision; ka1k: the configuration's FP64). Every rank runs its own
+    # system; the ensemble's replicas are split over the ranks (greedy N-balanced partition).
+    prec = wk.get("prec", "mixed")
+    subset = None
+    if wk["kind"] == "ensemble":
+        spec_all = wl.ensemble(wk["nrep"], wk["seed"])
+        subset = partition_replicas(spec_all.n, world)[rank]
+    s, n_sys, T = setup_system(kamd, wl, prec, dev, wk, subset=subset)
     if args.tuning:
         t4 = args.tuning.split(",")
         s.set_tuning(threads_per_atom=int(t4[0]), block_size=int(t4[1]), skin=float(t4[2]), skin_outer=float(t4[3]))
@@ -414,14 +507,16 @@ def main():
     times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush, step=stepper(s, T))
     clk = clocks.stop()
     total = max_over_ranks(float(times.sum()), dist, "cuda")
+    n_job = int(round(sum_over_ranks(n_sys, dist))) if dist else n_sys
     info = s.info()
     pairs = s.count_pairs()
     entries = info["list_entries"]
-    drift_mixed, fluct_mixed = drift_per_tau(log, wl.DT) if wk["timed"] == "nve" else (None, None)
-    value = whole_job_rate(world, n_sys, CHUNK * args.steps, total)
-    pair_evals = entries * CHUNK * args.steps * world / total
+    pairs_job = sum_over_ranks(pairs, dist) if dist else pairs
+    drift_main = drift_stats(log, wl.DT) if wk["timed"] == "nve" else None
+    value = n_job * CHUNK * args.steps / total
+    pair_evals = (sum_over_ranks(entries, dist) if dist else entries) * CHUNK * args.steps / total
     flop_step = FLOP_PAIR_IN * 2 * pairs + FLOP_PAIR_OUT * (entries - 2 * pairs)
-    launch_s = total / args.steps
+    launch_s = float(times.sum()) / args.steps
     achieved = flop_step * CHUNK / launch_s / 1e12
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * FP32_LANES_PER_SM * nsm * SM_MAX_MHZ * 1e6 / 1e12
@@ -431,22 +526,26 @@ def main():
     if not args.no_e2e:
         e2e_steps = max(3, min(args.steps, 20))
         e2e_el, h2d, d2h = run_e2e(torch, kamd, s, wl.DT, e2e_steps, None if wk["timed"] in ("nve", "ladder") else T)
-        e2e = {"value": world * n_sys * CHUNK * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e_el = max_over_ranks(e2e_el, dist, "cuda")
+        e2e = {"value": n_job * CHUNK * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     s.close()
 
-    # ---- all-FP64 GPU path on the same protocol (context for the mixed number)
+    # ---- all-FP64 GPU path on the same protocol and window (the context of the metric: mixed vs FP64
+    # at equal or better drift)
     fp64 = None
-    k64 = args.fp64_steps if args.fp64_steps is not None else (max(3, min(args.steps, 20))
-                                                                if args.workload == "ka32k" else 0)
-    if rank == 0 and k64 > 0:
-        s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk)
+    k64 = args.fp64_steps if args.fp64_steps is not None else (args.steps if args.workload == "ka32k" else 0)
+    if rank == 0 and k64 > 0 and prec == "mixed":
+        s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk, subset=subset)
         if not args.no_autotune:
             s64.autotune(wl.DT, probe_steps=50 if n_sys < 200000 else 10, skin=wk.get("skin"))
         t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
-        d64, f64 = drift_per_tau(log64, wl.DT) if wk["timed"] == "nve" else (None, None)
+        d64 = drift_stats(log64, wl.DT) if wk["timed"] == "nve" else None
         fp64 = {"value": n_sys * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
-                "drift_per_particle_per_tau": d64, "etot_fluct_per_particle": f64,
+                "drift_per_particle_per_tau": d64["slope"] if d64 else None,
+                "drift_err": d64["err"] if d64 else None,
+                "drift_window_steps": d64["window_steps"] if d64 else None,
+                "etot_fluct_per_particle": d64["rms"] if d64 else None,
                 "tuning": s64.tuning}
         s64.close()
 
@@ -456,27 +555,39 @@ def main():
             dist.destroy_process_group()
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl)
+    eq_better = drift_equal_or_better(drift_main, {"slope": fp64["drift_per_particle_per_tau"],
+                                                   "err": fp64["drift_err"]} if fp64 else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wk["desc"], "n": n_sys, "md_steps_per_bench_step": CHUNK,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "strong" if wk["kind"] == "ensemble" else "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": wk["desc"], "n": n_job, "md_steps_per_bench_step": CHUNK,
                    "timed_md_steps": CHUNK * args.steps,
-                   "precision": "mixed: 64-bit fixed-point positions, FP32 velocities/forces/pair math, "
-                                "FP64 reductions",
+                   "precision": ("FP64 positions, velocities, forces and pair math" if prec == "fp64" else
+                                 "mixed: 64-bit fixed-point positions, FP32 velocities/forces/pair math, "
+                                 "FP64 reductions"),
                    "l2": "flushed between timed steps (256 MB write)", "tuning": tuning,
-                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+                   "parallelism": ("replicas split over ranks (greedy N-balanced)" if wk["kind"] == "ensemble"
+                                   else "replicas only") if world > 1 else "single GPU"},
         "pair_evals_per_s": pair_evals,
-        "useful_pair_evals_per_s": 2 * pairs * CHUNK * args.steps * world / total,
+        "useful_pair_evals_per_s": 2 * pairs_job * CHUNK * args.steps / total,
         "list_entries": entries, "pairs_within_cutoff": pairs,
-        "drift_per_particle_per_tau": drift_mixed, "etot_fluct_per_particle": fluct_mixed,
+        "drift_per_particle_per_tau": drift_main["slope"] if drift_main else None,
+        "drift_err": drift_main["err"] if drift_main else None,
+        "drift_window_steps": drift_main["window_steps"] if drift_main else None,
+        "etot_fluct_per_particle": drift_main["rms"] if drift_main else None,
+        "drift_note": ("slope of E_tot/N against t over the timed NVE window (thermo every 10 steps); err = "
+                       "moving-block bootstrap of the residuals (one run: does not include run-to-run scatter)"),
         "fp64": fp64,
         "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "drift_equal_or_better": eq_better,
+        "drift_equal_or_better_rule": "|d_mixed| <= |d_fp64| + 2 * hypot(err_mixed, err_fp64)",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.workload, tuning),
                      "frac_at_measured_clock": (achieved / (peak * clk["sm_mhz"] / SM_MAX_MHZ)
                                                 if clk.get("sm_mhz") else None),
-                     "kernel": "md_persistent<mixed> (one launch = 100 MD steps)",
+                     "kernel": f"md_persistent<{'fp64' if prec == 'fp64' else 'mixed'}> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
         "analysis_ms": analysis,
         "device_bytes": device_bytes,

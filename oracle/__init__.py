@@ -12,6 +12,9 @@ function cites the passage of the paper it restates:
 * ``forces`` -- Eq. (KAFix) with Eq. (VshiftedKALJ), all pairs, half loop
   (Sec. "Accelerations"), minimum image by the branch rule (Sec. "Periodic
   boundary conditions").
+* ``forces_threads`` -- the same sum spread over host threads (per-thread
+  force arrays added in thread order), for timing on all cores and for long
+  runs; ``set_threads`` makes ``run`` use it.
 * ``force_on`` -- Eq. (KAFix) for one particle against every other particle.
 * ``run`` -- velocity Verlet (Eqs. (velVerletPos)/(velVerletVel)) in the order
   of Sec. "NVE molecular dynamics simulation"; the stochastic bath of Sec.
@@ -58,7 +61,9 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
            "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP for the threaded force sum; without it that routine runs on one thread
+    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -81,6 +86,9 @@ def _load():
         lib.ora_draw_jitter3.restype = None
         lib.ora_forces.argtypes = [i64, d, i32, c_int, d, d, d, dbl, d, d, d]
         lib.ora_force_on.argtypes = [i64, i64, d, i32, c_int, d, d, d, dbl, d, d]
+        lib.ora_forces_threads.argtypes = [i64, d, i32, c_int, d, d, d, dbl, d, d, d, c_int]
+        lib.ora_set_threads.argtypes = [c_int]
+        lib.ora_max_threads.argtypes = []
         lib.ora_maxwell_boltzmann.argtypes = [i64, dbl, dbl, u64, u64, i32, d]
         lib.ora_init_lattice.argtypes = [i64, dbl, dbl, dbl, dbl, u64, d, d]
         lib.ora_run.argtypes = [i64, d, d, d, i32, i32, c_int, d, d, d, dbl, dbl, dbl, i64, i64,
@@ -88,7 +96,7 @@ def _load():
         lib.ora_rdf.argtypes = [i64, d, i32, dbl, dbl, i64, d]
         lib.ora_msd.argtypes = [i64, d, i32, d, i32, c_int, dbl, d]
         for name in ("ora_forces", "ora_force_on", "ora_maxwell_boltzmann", "ora_init_lattice",
-                     "ora_run", "ora_rdf", "ora_msd"):
+                     "ora_run", "ora_rdf", "ora_msd", "ora_forces_threads", "ora_set_threads", "ora_max_threads"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -163,6 +171,32 @@ def forces(pos, types, params: Params, L):
                             _dp(params.rc), float(L), _dp(f), ctypes.byref(pe), ctypes.byref(vir))
     _check(rc, "forces")
     return f, pe.value, vir.value
+
+
+def forces_threads(pos, types, params: Params, L, nthreads):
+    """The all-pairs sum of ``forces`` over nthreads host threads (per-thread force arrays added
+    in thread order: reproducible for a fixed thread count; one thread is ``forces`` bitwise)."""
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    t = _i32(types)
+    f = np.zeros((n, 3))
+    pe = ctypes.c_double()
+    vir = ctypes.c_double()
+    rc = _load().ora_forces_threads(n, _dp(pos), _ip(t), params.ntypes, _dp(params.eps), _dp(params.sig),
+                                    _dp(params.rc), float(L), _dp(f), ctypes.byref(pe), ctypes.byref(vir),
+                                    int(nthreads))
+    _check(rc, "forces_threads")
+    return f, pe.value, vir.value
+
+
+def set_threads(nthreads):
+    """Host threads for the force sums inside ``run`` (1 = the single-thread oracle)."""
+    _check(_load().ora_set_threads(int(nthreads)), "set_threads")
+
+
+def max_threads():
+    """Threads OpenMP would use by default (1 when the oracle was built without OpenMP)."""
+    return int(_load().ora_max_threads())
 
 
 def force_on(pos, types, params: Params, L, i):

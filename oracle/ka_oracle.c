@@ -39,6 +39,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- Philox */
 
@@ -208,6 +211,96 @@ int ora_forces(int64_t n, const double *pos, const int32_t *types, int ntypes,
     if (pe) *pe = V;
     if (virial) *virial = W;
     return 0;
+}
+
+/* The same all-pairs sum spread over nthreads host threads (OpenMP): thread
+ * t takes the rows i = t, t + nthreads, ... of the half loop and adds its
+ * pair terms to a force array of its own; the arrays, energies and virials
+ * are then added in thread order 0, 1, ..., so the result is the same on
+ * every run with the same thread count. With one thread every sum is formed
+ * in the order of ora_forces, bitwise. Without OpenMP the pragmas are
+ * ignored and the loop runs on one thread (the result for nthreads > 1 is
+ * then the one-thread result). */
+int ora_forces_threads(int64_t n, const double *pos, const int32_t *types, int ntypes,
+                       const double *eps, const double *sig, const double *rc, double L,
+                       double *f, double *pe, double *virial, int nthreads)
+{
+    if (n < 0 || !pos || !types || !f || nthreads < 1) return -1;
+    int e = ora_check_tables(ntypes, eps, sig, rc, L);
+    if (e) return e;
+#ifndef _OPENMP
+    nthreads = 1;
+#endif
+    double *ft = (double *)calloc((size_t)nthreads * 3 * (size_t)n + 1, sizeof(double));
+    double *vt = (double *)calloc((size_t)nthreads * 2, sizeof(double));
+    if (!ft || !vt) { free(ft); free(vt); return -5; }
+#pragma omp parallel num_threads(nthreads)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *fl = ft + (size_t)t * 3 * (size_t)n;
+        double V = 0.0, W = 0.0;
+        for (int64_t i = t; i + 1 < n; i += nthreads) {
+            for (int64_t j = i + 1; j < n; ++j) {
+                double dx = ora_min_image(pos[3 * i + 0] - pos[3 * j + 0], L);
+                double dy = ora_min_image(pos[3 * i + 1] - pos[3 * j + 1], L);
+                double dz = ora_min_image(pos[3 * i + 2] - pos[3 * j + 2], L);
+                double r2 = dx * dx + dy * dy + dz * dz;
+                int tt = types[i] * ntypes + types[j];
+                if (r2 < rc[tt] * rc[tt]) {
+                    double v, fs;
+                    ora_pair(types[i], types[j], ntypes, eps, sig, rc, r2, &v, &fs);
+                    V += v;
+                    W += fs * r2;
+                    fl[3 * i + 0] += fs * dx; fl[3 * j + 0] -= fs * dx;
+                    fl[3 * i + 1] += fs * dy; fl[3 * j + 1] -= fs * dy;
+                    fl[3 * i + 2] += fs * dz; fl[3 * j + 2] -= fs * dz;
+                }
+            }
+        }
+        vt[2 * t] = V;
+        vt[2 * t + 1] = W;
+    }
+    double V = 0.0, W = 0.0;
+    for (int64_t k = 0; k < 3 * n; ++k) {
+        double s = 0.0;
+        for (int t = 0; t < nthreads; ++t) s += ft[(size_t)t * 3 * (size_t)n + (size_t)k];
+        f[k] = s;
+    }
+    for (int t = 0; t < nthreads; ++t) { V += vt[2 * t]; W += vt[2 * t + 1]; }
+    free(ft);
+    free(vt);
+    if (pe) *pe = V;
+    if (virial) *virial = W;
+    return 0;
+}
+
+/* Host threads used by the force sums of ora_run (1: ora_forces itself). */
+static int ora_run_threads = 1;
+int ora_set_threads(int nthreads)
+{
+    if (nthreads < 1) return -1;
+    ora_run_threads = nthreads;
+    return 0;
+}
+int ora_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Forces of ora_run: the single-thread oracle, or its threaded form. */
+static int ora_run_forces(int64_t n, const double *pos, const int32_t *types, int ntypes,
+                          const double *eps, const double *sig, const double *rc, double L,
+                          double *f, double *pe, double *virial)
+{
+    if (ora_run_threads <= 1) return ora_forces(n, pos, types, ntypes, eps, sig, rc, L, f, pe, virial);
+    return ora_forces_threads(n, pos, types, ntypes, eps, sig, rc, L, f, pe, virial, ora_run_threads);
 }
 
 /* Force on one particle i from all j != i (Eq. (KAFix) summed over every
@@ -390,7 +483,7 @@ int ora_run(int64_t n, double *pos, double *vel, double *f, int32_t *img,
                 }
             double lns_new = lns + xi * dt + 0.5 * g * dt * dt;
             double xi_a = xi + dt * g;
-            e = ora_forces(n, pos, types, ntypes, eps, sig, rc, L, fn, &pe, &W);
+            e = ora_run_forces(n, pos, types, ntypes, eps, sig, rc, L, fn, &pe, &W);
             if (e) { free(fn); return e; }
             for (int64_t i = 0; i < n; ++i)
                 for (int c = 0; c < 3; ++c) {
@@ -415,7 +508,7 @@ int ora_run(int64_t n, double *pos, double *vel, double *f, int32_t *img,
                     pos[3 * i + c] = x;
                 }
             for (int64_t i = 0; i < 3 * n; ++i) vel[i] += 0.5 * (f[i] / mass) * dt;
-            e = ora_forces(n, pos, types, ntypes, eps, sig, rc, L, f, &pe, &W);
+            e = ora_run_forces(n, pos, types, ntypes, eps, sig, rc, L, f, &pe, &W);
             if (e) { free(fn); return e; }
             for (int64_t i = 0; i < 3 * n; ++i) vel[i] += 0.5 * (f[i] / mass) * dt;
             if (kind == ORA_RESAMPLE && step % nstep_boltz == 0) {

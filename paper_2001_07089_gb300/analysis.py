@@ -115,3 +115,68 @@ def cooling_ladder(system: "kamd.System", temperatures, dt: float, n_bath: int, 
         prod = production(system, T) if production is not None else system.step_nve(dt, n_prod, log_every=log_every)
         stages.append({"T": T, "bath": bath, "nve": nve, "production": prod})
     return stages
+
+
+# ------------------------------------------------------------------ statistics of long runs
+
+def drift_fit(t, e, block=None, nboot=400, seed=12345) -> dict:
+    """Energy drift of an NVE run: least-squares slope of e(t) with a moving-block bootstrap error.
+
+    The residuals about the fitted line are correlated in time, so the error
+    bar resamples them in overlapping blocks of `block` consecutive samples
+    (default: 1/10 of the series, at least 2; Kunsch's moving-block
+    bootstrap), adds them back to the fitted line and refits; the error is the
+    standard deviation of the refitted slopes. Also returned: the RMS residual
+    (the size of the energy fluctuations about the trend).
+    """
+    t = np.asarray(t, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    n = len(e)
+    if n < 4 or len(t) != n:
+        return {"slope": None, "err": None, "rms": None, "n": n}
+    A = np.vstack([t, np.ones_like(t)]).T
+    coef, *_ = np.linalg.lstsq(A, e, rcond=None)
+    fit = A @ coef
+    res = e - fit
+    b = int(block) if block else max(2, n // 10)
+    b = min(max(b, 1), n)
+    rng = np.random.default_rng(seed)
+    nblk = -(-n // b)
+    starts = rng.integers(0, n - b + 1, size=(nboot, nblk))
+    idx = (starts[:, :, None] + np.arange(b)[None, None, :]).reshape(nboot, -1)[:, :n]
+    boot = fit[None, :] + res[idx]
+    # slope of each resampled series (closed-form least squares against the same t)
+    tc = t - t.mean()
+    slopes = (boot - boot.mean(axis=1, keepdims=True)) @ tc / np.dot(tc, tc)
+    return {"slope": float(coef[0]), "err": float(np.std(slopes, ddof=1)), "rms": float(np.std(res)), "n": n}
+
+
+def block_mean(samples, nblocks: int):
+    """Mean over axis 0 and its standard error from `nblocks` contiguous blocks (block averaging).
+
+    Block means of a correlated series are nearly independent once a block is
+    longer than the correlation time; the error is std(block means)/sqrt(nblocks).
+    """
+    x = np.asarray(samples, dtype=np.float64)
+    m = (x.shape[0] // nblocks) * nblocks
+    if nblocks < 2 or m == 0:
+        raise ValueError("need at least 2 blocks of one sample")
+    blocks = x[:m].reshape((nblocks, m // nblocks) + x.shape[1:]).mean(axis=1)
+    return blocks.mean(axis=0), blocks.std(axis=0, ddof=1) / np.sqrt(nblocks)
+
+
+def msd_time_origins(unwrapped, types, ntypes: int, lags, origin_every: int = 1) -> np.ndarray:
+    """Per-type MSD (Eq. (msdwithi)) at the frame lags `lags`, averaged over time origins.
+
+    unwrapped: [frames, n, 3] unwrapped positions; origins every `origin_every`
+    frames, each lag averaged over the origins that fit. Returns [len(lags), ntypes].
+    """
+    x = np.asarray(unwrapped, dtype=np.float64)
+    types = np.asarray(types)
+    out = np.zeros((len(lags), ntypes))
+    for k, lag in enumerate(lags):
+        orig = np.arange(0, x.shape[0] - lag, origin_every)
+        d2 = np.sum((x[orig + lag] - x[orig]) ** 2, axis=2)  # [origins, n]
+        for a in range(ntypes):
+            out[k, a] = d2[:, types == a].mean()
+    return out

@@ -98,3 +98,62 @@ def test_cooling_ladder_runs_bath_nve_production_per_temperature():
     seen = []
     analysis.cooling_ladder(_Recorder(), [2.0, 1.0], 0.005, 10, 10, 10, production=lambda s, T: seen.append(T) or T)
     assert seen == [2.0, 1.0]
+
+
+# ------------------------------------------------------------------ long-run statistics
+
+def _ar1(n, phi, sigma, rng):
+    x = np.zeros(n)
+    z = rng.normal(0.0, sigma, size=n)
+    for k in range(1, n):
+        x[k] = phi * x[k - 1] + z[k]
+    return x
+
+
+def test_drift_fit_error_bar_is_calibrated_on_correlated_noise():
+    """A known slope under strongly correlated (AR(1), phi = 0.95) noise: over many independent
+    series the bootstrap error bar matches the actual scatter of the fitted slopes (within 35 %),
+    and about 95 % of fits lie within 2 error bars of the true slope. A bar that ignored the
+    correlation (plain least squares) would be several times too small and fail both."""
+    rng = np.random.default_rng(3)
+    t = np.arange(1000) * 0.05
+    slope = 2e-5
+    fits = []
+    for _ in range(200):
+        e = -5.0 + slope * t + _ar1(len(t), 0.95, 1e-5, rng)
+        fits.append(analysis.drift_fit(t, e, nboot=200, seed=int(rng.integers(1 << 30))))
+    s = np.array([f["slope"] for f in fits])
+    err = np.array([f["err"] for f in fits])
+    assert 0.65 < np.median(err) / np.std(s) < 1.35
+    inside = np.mean(np.abs(s - slope) <= 2 * err)
+    assert 0.85 <= inside <= 0.995
+    # no trend: zero within the bar; too short a series: no fit
+    f0 = analysis.drift_fit(t, -5.0 + _ar1(len(t), 0.9, 1e-5, rng))
+    assert abs(f0["slope"]) < 4 * f0["err"]
+    assert analysis.drift_fit(t[:3], t[:3])["slope"] is None
+
+
+def test_block_mean_error_of_independent_samples():
+    rng = np.random.default_rng(5)
+    x = rng.normal(2.0, 0.5, size=(20000, 3))
+    m, e = analysis.block_mean(x, 20)
+    assert np.allclose(m, 2.0, atol=4 * 0.5 / np.sqrt(20000))
+    assert np.all((e > 0.5 * 0.5 / np.sqrt(20000)) & (e < 1.6 * 0.5 / np.sqrt(20000)))
+    with pytest.raises(ValueError):
+        analysis.block_mean(x[:1], 2)
+
+
+def test_msd_over_time_origins_of_ballistic_particles():
+    """Particles moving at constant velocity: MSD(lag) = <v^2> (lag dt)^2 per type, for any origin."""
+    rng = np.random.default_rng(7)
+    n, frames, dt = 50, 40, 0.1
+    v = rng.normal(size=(n, 3))
+    x0 = rng.uniform(0, 10, size=(n, 3))
+    types = np.array([0] * 30 + [1] * 20)
+    traj = x0[None] + v[None] * (np.arange(frames) * dt)[:, None, None]
+    lags = [1, 5, 20]
+    m = analysis.msd_time_origins(traj, types, 2, lags, origin_every=3)
+    v2 = np.sum(v * v, axis=1)
+    for k, lag in enumerate(lags):
+        assert m[k, 0] == pytest.approx(v2[:30].mean() * (lag * dt) ** 2, rel=1e-12)
+        assert m[k, 1] == pytest.approx(v2[30:].mean() * (lag * dt) ** 2, rel=1e-12)

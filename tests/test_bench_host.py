@@ -74,3 +74,35 @@ def test_committed_summaries_carry_the_fields_the_bench_reads():
         for key in ("kernel_sources_sha256", "tuning", "dram_bytes_per_launch"):
             assert f"- `{key}`: `" in text, (n, key)
         assert "--clock-control none" in text
+
+
+def test_drift_equal_or_better_rule():
+    a = {"slope": 1e-6, "err": 1e-7}
+    assert bench.drift_equal_or_better(a, {"slope": -2e-6, "err": 1e-7}) is True
+    assert bench.drift_equal_or_better({"slope": 5e-6, "err": 1e-7}, {"slope": 1e-6, "err": 1e-7}) is False
+    # within two combined error bars counts as equal
+    assert bench.drift_equal_or_better({"slope": 1.2e-6, "err": 1e-7}, {"slope": 1e-6, "err": 1e-7}) is True
+    assert bench.drift_equal_or_better(None, a) is None
+
+
+def test_drift_stats_window_and_error():
+    dt = 0.005
+    steps = np.arange(10, 2010, 10)
+    rng = np.random.default_rng(1)
+    e = -5.4 + 3e-6 * steps * dt + rng.normal(0, 1e-5, size=len(steps))
+    d = bench.drift_stats(_log(steps, e), dt)
+    assert d["window_steps"] == 1990
+    assert abs(d["slope"] - 3e-6) < 4 * d["err"] and 0 < d["err"] < 1e-5
+    assert bench.drift_stats(_log([10, 20, 30], [0.0, 1.0, 2.0]), dt)["slope"] is None
+
+
+def test_replica_partition_is_complete_disjoint_and_balanced():
+    from paper_2001_07089_gb300 import workloads as wl
+    n = wl.ensemble(512, 4).n
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.partition_replicas(n, world)
+        flat = sorted(r for p in parts for r in p)
+        assert flat == list(range(len(n)))
+        loads = [int(n[p].sum()) for p in parts]
+        assert max(loads) - min(loads) <= int(n.max())
+        assert all(p == sorted(p) for p in parts)

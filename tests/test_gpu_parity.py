@@ -174,8 +174,34 @@ def test_nve_100_steps_energies(prec):
     assert thermo_rel(log, ref["thermo"], "etot_per_n", 4) <= tol
     assert thermo_rel(log, ref["thermo"], "pe_per_n", 2) <= tol
     assert thermo_rel(log, ref["thermo"], "ke_per_n", 3) <= tol
+    # PE and KE each against their own magnitude
+    assert own_rel(log, ref["thermo"], "pe_per_n", 2) <= tol
+    assert own_rel(log, ref["thermo"], "ke_per_n", 3) <= tol
     d = np.abs(min_image_diff(p, ref["pos"], L))
     assert d.max() < (1e-9 if prec == "fp64" else 1e-3)
+
+
+def own_rel(gpu_log, ref_thermo, field_gpu, col):
+    """Largest per-step error of one thermo field relative to that field's own magnitude."""
+    a = gpu_log[field_gpu][:, 0]
+    b = ref_thermo[:, col]
+    return np.max(np.abs(a - b) / np.abs(b))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nve_100_steps_at_T08_plain_relative_energies(prec):
+    """The 32k configuration's temperature, T = 0.8, where E_tot/N (about -5.4) is far from zero:
+    E_tot, PE and KE per step each within the plain relative tolerance |dE|/|E| over 100 steps."""
+    pos, vel, types, L = melted(1000, 34, nsteps=300, T0=0.8)
+    ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 100, log_every=1)
+    th = ref["thermo"]
+    assert np.all(np.abs(th[:, 4]) > 3.0)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        log = s.step_nve(0.005, 100, log_every=1)
+    tol = 1e-10 if prec == "fp64" else TOL_E["mixed"]
+    for field, col in (("etot_per_n", 4), ("pe_per_n", 2), ("ke_per_n", 3)):
+        assert own_rel(log, th, field, col) <= tol, field
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -534,21 +560,65 @@ def test_cooling_ladder_batch_matches_standalone_and_oracle():
         off += n
 
 
+def rdf_counts(g, types, L, dr, nbins):
+    """Pair counts per bin behind normalised partial g(r) rows (AA, BB, AB): the inverse of the
+    normalisation of Sec. "Radial distribution function with Python" (like pairs counted twice)."""
+    na = int(np.sum(np.asarray(types) == 0))
+    nb = len(types) - na
+    k = np.arange(nbins)
+    shell = 4.0 / 3.0 * np.pi * ((k + 1) ** 3 - k ** 3) * dr ** 3
+    V = L ** 3
+    h = np.stack([g[0] * shell * na * (na - 1) / V, g[1] * shell * nb * (nb - 1) / V, g[2] * shell * na * nb / V])
+    c = np.rint(h)
+    assert np.max(np.abs(h - c)) < 1e-6 * max(1.0, c.max())
+    return c.astype(np.int64)
+
+
+def bin_edge_allowance(pos, types, L, dr, nbins, tol):
+    """Per-bin count difference allowed for pairs whose distance lies within tol of a bin edge
+    (either side may bin them on either side of it), and the number of such pairs."""
+    pos = np.asarray(pos)
+    t = np.asarray(types)
+    allow = np.zeros((3, nbins), dtype=np.int64)
+    nedge = 0
+    for i in range(len(pos) - 1):
+        d = pos[i] - pos[i + 1:]
+        d -= L * np.rint(d / L)
+        r = np.sqrt(np.sum(d * d, axis=1))
+        x = r / dr
+        k = np.rint(x).astype(np.int64)
+        near = (np.abs(x - k) * dr < tol) & (k >= 0) & (k <= nbins)
+        for j in np.nonzero(near)[0]:
+            ti, tj = t[i], t[i + 1 + j]
+            row = 0 if ti == tj == 0 else (1 if ti == tj == 1 else 2)
+            w = 2 if ti == tj else 1
+            for kk in (k[j] - 1, k[j]):
+                if 0 <= kk < nbins:
+                    allow[row, kk] += w
+            nedge += 1
+    return allow, nedge
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_rdf_and_msd_match_oracle(prec):
+    """g(r) bin by bin: both sides bin the same pair distances (the GPU's mixed path from the exact
+    64-bit fixed-point differences, the oracle from the read-back doubles), so the pair counts behind
+    every bin agree exactly except for pairs within 1e-12 L of a bin edge, which the test counts."""
     pos, vel, types, L = melted(1000, 91, nsteps=100)
+    dr, nbins = 0.05, 80
     with make_system(1000, L, types, prec) as s:
         s.set_state(pos, vel)
         s.step_nve(0.005, 100)
-        g = s.rdf(0.05, 80, reset=True)
+        g = s.rdf(dr, nbins, reset=True)
         p, v, img = s.get_state()
         msd = s.msd()
-    g_ref = oracle.rdf(p, types, L, 0.05, 80)
+    g_ref = oracle.rdf(p, types, L, dr, nbins)
     if prec == "fp64":
         assert np.allclose(g, g_ref, rtol=1e-12, atol=1e-12)
-    else:
-        # fixed-point distances may move a pair across a bin edge: compare totals and shape
-        assert np.max(np.abs(g - g_ref)) < 0.05 * np.max(g_ref)
+    cg, cr = rdf_counts(g, types, L, dr, nbins), rdf_counts(g_ref, types, L, dr, nbins)
+    allow, nedge = bin_edge_allowance(p, types, L, dr, nbins, 1e-12 * L)
+    assert np.all(np.abs(cg - cr) <= allow), (np.abs(cg - cr).max(), nedge)
+    assert cg.sum() == cr.sum() or nedge > 0
     m_ref = oracle.msd(p, img, pos, types, 2, L)
     assert np.allclose(msd, m_ref, rtol=1e-9 if prec == "fp64" else 1e-5)
 

@@ -151,6 +151,58 @@ def test_newton_third_law_and_translation_invariance():
     assert abs(w2 - w) < 1e-10 * abs(w)
 
 
+def test_force_on_is_row_of_all_pairs_sum_and_gradient():
+    """ora_force_on (particle i against every other particle, O(N)) is what the large-N GPU
+    checks compare against. On a melted N = 500 liquid it gives row i of the all-pairs forces for
+    every i, its half pair energies add up to V, and for sampled particles it equals the
+    central-difference gradient -dV/dr_i of the total energy (Eq. (KAFix) as the gradient of
+    Eq. (VshiftedKALJ)), so a dropped 1/2, a swapped i/j in the minimum image or a skipped j
+    fails here."""
+    pos, vel, types, L = melted(500, 19, nsteps=100)
+    f, v, w = oracle.forces(pos, types, ka_params(), L)
+    frms = np.sqrt(np.mean(np.sum(f * f, axis=1)))
+    fo = np.zeros_like(f)
+    vhalf = np.zeros(len(pos))
+    for i in range(len(pos)):
+        fo[i], vhalf[i] = oracle.force_on(pos, types, ka_params(), L, i)
+    assert np.max(np.linalg.norm(fo - f, axis=1)) <= 1e-13 * frms
+    assert vhalf.sum() == pytest.approx(v, rel=1e-13)
+    h = 1e-6
+    for i in (0, 137, 499):
+        for c in range(3):
+            p1 = pos.copy(); p1[i, c] += h
+            p2 = pos.copy(); p2[i, c] -= h
+            g = -(oracle.forces(p1, types, ka_params(), L)[1] - oracle.forces(p2, types, ka_params(), L)[1]) / (2 * h)
+            assert abs(fo[i, c] - g) <= 1e-6 * frms
+
+
+@pytest.mark.parametrize("a,b", [(0, 0), (0, 1), (1, 1)])
+def test_force_on_pair_minimum_and_far_image(a, b):
+    """Two particles at 2^(1/6) sigma_ab: force_on gives F = 0 on both and half the shifted
+    depth -eps - V(r_c) each; placed across the periodic boundary the pair is found through its
+    minimum image; beyond r_c it gives exactly nothing."""
+    eps, sig = wl.KA_EPS[a, b], wl.KA_SIG[a, b]
+    rmin = 2.0 ** (1.0 / 6.0) * sig
+    vc = 4.0 * eps * (2.5 ** -12 - 2.5 ** -6)
+    L = 20.0
+    types = np.array([a, b], dtype=np.int32)
+    for x0 in (5.0, L - 0.5 * rmin):  # second case: the pair straddles x = L
+        pos = np.array([[x0, 3.0, 4.0], [np.mod(x0 + rmin, L), 3.0, 4.0]])
+        for i in (0, 1):
+            fi, vh = oracle.force_on(pos, types, ka_params(), L, i)
+            assert np.all(np.abs(fi) < 1e-12 * eps / sig)
+            assert vh == pytest.approx(0.5 * (-eps - vc), rel=1e-13)
+    pos = np.array([[5.0, 3.0, 4.0], [5.0, 3.0 + 2.5 * sig * (1 + 1e-9), 4.0]])
+    fi, vh = oracle.force_on(pos, types, ka_params(), L, 0)
+    assert np.all(fi == 0.0) and vh == 0.0
+    # inside the cutoff but off the minimum: F on i points along r_i - r_j with Eq. (KAFix)'s sign
+    pos = np.array([[5.0, 3.0, 4.0], [5.0 + 1.3 * sig, 3.0, 4.0]])
+    fi, _ = oracle.force_on(pos, types, ka_params(), L, 0)
+    r = 1.3 * sig
+    fmag = 48 * eps * (sig ** 12 / r ** 13 - 0.5 * sig ** 6 / r ** 7)
+    assert fi[0] == pytest.approx(-fmag, rel=1e-13) and fi[1] == 0.0 and fi[2] == 0.0
+
+
 def test_perfect_lattice_zero_force_and_lattice_sum():
     """A perfect simple-cubic A lattice: F_i = 0 by symmetry; V/N = half the lattice sum over shells."""
     m = 8
@@ -411,3 +463,33 @@ def test_waiting_time_msd_free_flight():
         t = 100 * dt
         assert msd[0] == pytest.approx(v2[:2].mean() * t * t, rel=1e-12)
         assert msd[1] == pytest.approx(v2[2:].mean() * t * t, rel=1e-12)
+
+
+# ------------------------------------------------------------- threaded sum
+
+def test_threaded_force_sum_reproducible_and_equal_to_serial():
+    """The threaded all-pairs sum (per-thread force arrays added in thread order): one thread is the
+    serial oracle bitwise; a fixed thread count gives bitwise identical results on every call; any
+    thread count agrees with the serial sum to rounding; a run with threads follows the serial run."""
+    pos, vel, types, L = melted(1000, 35, nsteps=50)
+    f, v, w = oracle.forces(pos, types, ka_params(), L)
+    f1, v1, w1 = oracle.forces_threads(pos, types, ka_params(), L, 1)
+    assert np.array_equal(f, f1) and v == v1 and w == w1
+    frms = np.sqrt(np.mean(np.sum(f * f, axis=1)))
+    for nt in (2, 3, 8):
+        fa, va, wa = oracle.forces_threads(pos, types, ka_params(), L, nt)
+        fb, vb, wb = oracle.forces_threads(pos, types, ka_params(), L, nt)
+        assert np.array_equal(fa, fb) and va == vb and wa == wb
+        assert np.max(np.abs(fa - f)) < 1e-13 * frms
+        assert abs(va - v) < 1e-13 * abs(v) and abs(wa - w) < 1e-13 * abs(w)
+    serial = oracle.run(pos, vel, types, ka_params(), L, 0.005, 20, log_every=1)
+    try:
+        oracle.set_threads(4)
+        par = oracle.run(pos, vel, types, ka_params(), L, 0.005, 20, log_every=1)
+        oracle.set_threads(1)
+        again = oracle.run(pos, vel, types, ka_params(), L, 0.005, 20, log_every=1)
+    finally:
+        oracle.set_threads(1)
+    scale = np.maximum(np.abs(serial["thermo"]), 1.0)
+    assert np.max(np.abs(par["thermo"] - serial["thermo"]) / scale) < 1e-12
+    assert np.array_equal(again["thermo"], serial["thermo"])
