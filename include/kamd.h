@@ -138,6 +138,28 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per,
                           double mass, double skin, md_precision prec, void* stream,
                           md_system** out);
 
+/*
+ * md_create_batch_dim: as md_create_batch, in ndim = 3 or 2 dimensions. The
+ * two-dimensional model is the Kob-Andersen problem of Sec. "Suggested
+ * problems" (e.g. N = 1000 at N/L^2 = 1.204, L = 28.82, A:B = 65:35): every
+ * particle lies in the plane z = L/2 of the cubic box and keeps v_z = 0
+ * (md_set_state ignores the z coordinates and z velocities it is given, and
+ * md_get_state returns z = L/2, v_z = 0); every pair then has dz = 0, so the
+ * forces stay in the plane. Wherever the three-dimensional model counts 3N
+ * degrees of freedom the two-dimensional one counts 2N: the temperature of
+ * Eq. (equip3N) (3 replaced by 2, as the problem says), the Maxwell-Boltzmann
+ * rescale, X and the bath mass Q = X T tau^2 of Nose-Hoover. md_rdf
+ * normalises by the ring area pi((k+1)^2 - k^2) dr^2 and V = L^2;
+ * md_init_lattice uses a square lattice of m = ceil(n^(1/2)) sites per edge
+ * in the plane (no z jitter). ndim = 3 is md_create_batch. MD_ERR_INVALID_ARG
+ * for any other ndim.
+ */
+md_status md_create_batch_dim(int ndim, int nrep, const int64_t* n_per, const double* L_per,
+                              const uint8_t* types, int ntypes,
+                              const double* eps, const double* sigma, const double* rc,
+                              double mass, double skin, md_precision prec, void* stream,
+                              md_system** out);
+
 /* md_set_state: overwrite positions and velocities (n_total*3 doubles each,
  * caller order; vel may be NULL for zero velocities). Clears image counters,
  * marks forces stale and forces a neighbour-list rebuild. */

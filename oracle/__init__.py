@@ -23,6 +23,10 @@ function cites the passage of the paper it restates:
   or (ridotsolved), (FoxAndersen_ydottplush)).
 * ``maxwell_boltzmann`` / ``init_lattice`` -- Sec. "Statistical temperature
   bath" steps 1-4 and Sec. "Initialization of positions".
+* ``ndim=2`` (``maxwell_boltzmann``, ``init_lattice``, ``run``, ``rdf``) -- the
+  two-dimensional problem of Sec. "Suggested problems": particles in the plane
+  z = L/2 with v_z = 0, 2 instead of 3 in Eq. (equip3N) (T, the velocity
+  rescale, X of the Nose-Hoover bath) and the shell area in g(r).
 * ``rdf`` / ``msd`` -- Eqs. (gAA)/(gAB) with the histogram normalisation of
   Sec. "Radial distribution function with Python"; Eqs. (msd)/(msdwithi).
 * ``philox4x32_10`` -- the counter-based generator of Salmon et al. (SC'11).
@@ -89,11 +93,11 @@ def _load():
         lib.ora_forces_threads.argtypes = [i64, d, i32, c_int, d, d, d, dbl, d, d, d, c_int]
         lib.ora_set_threads.argtypes = [c_int]
         lib.ora_max_threads.argtypes = []
-        lib.ora_maxwell_boltzmann.argtypes = [i64, dbl, dbl, u64, u64, i32, d]
-        lib.ora_init_lattice.argtypes = [i64, dbl, dbl, dbl, dbl, u64, d, d]
-        lib.ora_run.argtypes = [i64, d, d, d, i32, i32, c_int, d, d, d, dbl, dbl, dbl, i64, i64,
+        lib.ora_maxwell_boltzmann.argtypes = [i64, c_int, dbl, dbl, u64, u64, i32, d]
+        lib.ora_init_lattice.argtypes = [i64, c_int, dbl, dbl, dbl, dbl, u64, d, d]
+        lib.ora_run.argtypes = [i64, c_int, d, d, d, i32, i32, c_int, d, d, d, dbl, dbl, dbl, i64, i64,
                                 c_int, dbl, dbl, i64, u64, d, d, i64]
-        lib.ora_rdf.argtypes = [i64, d, i32, dbl, dbl, i64, d]
+        lib.ora_rdf.argtypes = [i64, c_int, d, i32, dbl, dbl, i64, d]
         lib.ora_msd.argtypes = [i64, d, i32, d, i32, c_int, dbl, d]
         for name in ("ora_forces", "ora_force_on", "ora_maxwell_boltzmann", "ora_init_lattice",
                      "ora_run", "ora_rdf", "ora_msd", "ora_forces_threads", "ora_set_threads", "ora_max_threads"):
@@ -211,26 +215,26 @@ def force_on(pos, types, params: Params, L, i):
     return f, pe.value
 
 
-def maxwell_boltzmann(n, T, seed, draw=0, mass=1.0, ids=None):
+def maxwell_boltzmann(n, T, seed, draw=0, mass=1.0, ids=None, ndim=3):
     vel = np.zeros((n, 3))
     keep = _i32(ids) if ids is not None else None
     idp = _ip(keep) if keep is not None else ctypes.POINTER(ctypes.c_int32)()
-    rc = _load().ora_maxwell_boltzmann(int(n), float(T), float(mass), int(seed), int(draw), idp, _dp(vel))
+    rc = _load().ora_maxwell_boltzmann(int(n), int(ndim), float(T), float(mass), int(seed), int(draw), idp, _dp(vel))
     _check(rc, "maxwell_boltzmann")
     return vel
 
 
-def init_lattice(n, L, T0, seed, jitter=0.05, mass=1.0):
+def init_lattice(n, L, T0, seed, jitter=0.05, mass=1.0, ndim=3):
     pos = np.zeros((n, 3))
     vel = np.zeros((n, 3))
-    rc = _load().ora_init_lattice(int(n), float(L), float(T0), float(mass), float(jitter), int(seed),
+    rc = _load().ora_init_lattice(int(n), int(ndim), float(L), float(T0), float(mass), float(jitter), int(seed),
                                   _dp(pos), _dp(vel))
     _check(rc, "init_lattice")
     return pos, vel
 
 
 def run(pos, vel, types, params: Params, L, dt, nsteps, kind=NVE, T_target=0.0, Q=0.0,
-        nstep_boltz=50, seed=0, state=None, forces_in=None, img=None, step0=0, log_every=1):
+        nstep_boltz=50, seed=0, state=None, forces_in=None, img=None, step0=0, log_every=1, ndim=3):
     """Advance (pos, vel) by nsteps; returns a dict with the new state and the thermo log.
 
     The inputs are copied, never modified. ``state`` = [xi, ln s] for Nose-Hoover.
@@ -247,7 +251,7 @@ def run(pos, vel, types, params: Params, L, dt, nsteps, kind=NVE, T_target=0.0, 
     st = np.array([0.0, 0.0] if state is None else state, dtype=np.float64)
     nlog = (nsteps // log_every) if log_every > 0 else 0
     thermo = np.zeros((max(nlog, 1), 8))
-    rc = _load().ora_run(n, _dp(pos), _dp(vel), _dp(f), _ip(img), _ip(t), params.ntypes,
+    rc = _load().ora_run(n, int(ndim), _dp(pos), _dp(vel), _dp(f), _ip(img), _ip(t), params.ntypes,
                          _dp(params.eps), _dp(params.sig), _dp(params.rc), float(L), params.mass,
                          float(dt), int(step0), int(nsteps), int(kind), float(T_target), float(Q),
                          int(nstep_boltz), int(seed), _dp(st), _dp(thermo), int(log_every))
@@ -273,10 +277,11 @@ def log_time_grid(n_md, t0=1.0, kmax=60):
     return out
 
 
-def rdf(pos, types, L, dr, nbins):
+def rdf(pos, types, L, dr, nbins, ndim=3):
     pos = _f64(pos, (-1, 3))
     g = np.zeros(3 * nbins)
-    rc = _load().ora_rdf(pos.shape[0], _dp(pos), _ip(_i32(types)), float(L), float(dr), int(nbins), _dp(g))
+    rc = _load().ora_rdf(pos.shape[0], int(ndim), _dp(pos), _ip(_i32(types)), float(L), float(dr), int(nbins),
+                         _dp(g))
     _check(rc, "rdf")
     return g.reshape(3, nbins)
 

@@ -336,23 +336,26 @@ int ora_force_on(int64_t n, int64_t i, const double *pos, const int32_t *types, 
 /* ------------------------------------------------------------ velocities */
 
 /* Maxwell-Boltzmann velocities at temperature T (k_B = 1, mass m) for the
- * particles [0, n): step 1 draw each component from a Gaussian of standard
- * deviation sqrt(T/m) (Eqs. (vxocitydistribution), (sigmavx)); step 3
- * subtract the mean velocity; step 4 rescale so that sum m v^2 = 3 n T
- * (Eq. (equip3N) with 3N degrees of freedom). Draw number d selects the
- * random stream (0 at initialisation, k for the k-th resampling). ids gives
- * each particle's index for the counter (NULL: its position in the array). */
-int ora_maxwell_boltzmann(int64_t n, double T, double mass, uint64_t seed, uint64_t d,
+ * particles [0, n) in ndim = 3 or 2 dimensions: step 1 draw each component
+ * from a Gaussian of standard deviation sqrt(T/m) (Eqs. (vxocitydistribution),
+ * (sigmavx)); in two dimensions v_z = 0 (the z draw is discarded, so x and y
+ * are the draws of the three-dimensional case); step 3 subtract the mean
+ * velocity; step 4 rescale so that sum m v^2 = ndim n T (Eq. (equip3N) with
+ * ndim N degrees of freedom; the 2-D problem of Sec. "Suggested problems"
+ * replaces 3 by 2 there). Draw number d selects the random stream (0 at
+ * initialisation, k for the k-th resampling). ids gives each particle's index
+ * for the counter (NULL: its position in the array). */
+int ora_maxwell_boltzmann(int64_t n, int ndim, double T, double mass, uint64_t seed, uint64_t d,
                           const int32_t *ids, double *vel)
 {
-    if (n < 1 || !(T >= 0.0) || !(mass > 0.0) || !vel) return -1;
+    if (n < 1 || (ndim != 2 && ndim != 3) || !(T >= 0.0) || !(mass > 0.0) || !vel) return -1;
     double sd = sqrt(T / mass);
     for (int64_t i = 0; i < n; ++i) {
         double g[3];
         ora_gauss3(seed, d, ids ? (uint32_t)ids[i] : (uint32_t)i, g);
         vel[3 * i + 0] = sd * g[0];
         vel[3 * i + 1] = sd * g[1];
-        vel[3 * i + 2] = sd * g[2];
+        vel[3 * i + 2] = ndim == 3 ? sd * g[2] : 0.0;
     }
     double mx = 0, my = 0, mz = 0;
     for (int64_t i = 0; i < n; ++i) { mx += vel[3 * i]; my += vel[3 * i + 1]; mz += vel[3 * i + 2]; }
@@ -361,7 +364,7 @@ int ora_maxwell_boltzmann(int64_t n, double T, double mass, uint64_t seed, uint6
     double s2 = 0;
     for (int64_t i = 0; i < n; ++i)
         s2 += mass * (vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] + vel[3 * i + 2] * vel[3 * i + 2]);
-    double scale = (s2 > 0.0) ? sqrt(3.0 * (double)n * T / s2) : 0.0;
+    double scale = (s2 > 0.0) ? sqrt((double)ndim * (double)n * T / s2) : 0.0;
     for (int64_t i = 0; i < 3 * n; ++i) vel[i] *= scale;
     return 0;
 }
@@ -371,15 +374,19 @@ int ora_maxwell_boltzmann(int64_t n, double T, double mass, uint64_t seed, uint6
  * kx fastest. When n < m^3, particle p takes site floor(p m^3 / n) (sites
  * spread evenly; for n = m^3 this is the paper's assignment). Each coordinate
  * is then moved by jitter * u with u uniform in (-1, 1) and wrapped into
- * [0, L). Velocities are Maxwell-Boltzmann at T0 (draw number 0). */
-int ora_init_lattice(int64_t n, double L, double T0, double mass, double jitter, uint64_t seed,
+ * [0, L). Velocities are Maxwell-Boltzmann at T0 (draw number 0).
+ * ndim = 2 (the 2-D problem of Sec. "Suggested problems"): the same on a
+ * square lattice of m = ceil(n^(1/2)) sites per edge in the plane z = L/2,
+ * which no particle leaves (z_i = v_iz = 0 relative to it); no z jitter. */
+int ora_init_lattice(int64_t n, int ndim, double L, double T0, double mass, double jitter, uint64_t seed,
                      double *pos, double *vel)
 {
-    if (n < 1 || !(L > 0.0) || !pos || !vel) return -1;
+    if (n < 1 || (ndim != 2 && ndim != 3) || !(L > 0.0) || !pos || !vel) return -1;
     int64_t m = 1;
-    while (m * m * m < n) ++m;
+    if (ndim == 3) while (m * m * m < n) ++m;
+    else while (m * m < n) ++m;
     double a = L / (double)m;
-    int64_t sites = m * m * m;
+    int64_t sites = ndim == 3 ? m * m * m : m * m;
     for (int64_t p = 0; p < n; ++p) {
         int64_t s = (int64_t)(((__int128)p * sites) / n);
         int64_t kx = s % m, ky = (s / m) % m, kz = s / (m * m);
@@ -387,7 +394,7 @@ int ora_init_lattice(int64_t n, double L, double T0, double mass, double jitter,
         ora_jitter3(seed, (uint32_t)p, u);
         double r[3] = {(0.5 + (double)kx) * a + jitter * u[0],
                        (0.5 + (double)ky) * a + jitter * u[1],
-                       (0.5 + (double)kz) * a + jitter * u[2]};
+                       ndim == 3 ? (0.5 + (double)kz) * a + jitter * u[2] : 0.5 * L};
         for (int c = 0; c < 3; ++c) {
             double x = r[c];
             if (x >= L) x -= L;
@@ -395,7 +402,7 @@ int ora_init_lattice(int64_t n, double L, double T0, double mass, double jitter,
             pos[3 * p + c] = x;
         }
     }
-    return ora_maxwell_boltzmann(n, T0, mass, seed, 0, NULL, vel);
+    return ora_maxwell_boltzmann(n, ndim, T0, mass, seed, 0, NULL, vel);
 }
 
 /* ------------------------------------------------------------- dynamics */
@@ -426,7 +433,9 @@ enum { ORA_NVE = 0, ORA_NOSE_HOOVER = 1, ORA_RESAMPLE = 2, ORA_NOSE_HOOVER_EXACT
 
 /*
  * Run nsteps of MD from (pos, vel) at time t; pos, vel, img are updated in
- * place. f (n*3) must hold F(x(t)) on entry and holds F at the end.
+ * place. ndim = 3, or 2 for the 2-D problem of Sec. "Suggested problems"
+ * (particles in one plane with v_z = 0, which the dynamics keeps: every pair
+ * has dz = 0, so F_z = 0; ndim N degrees of freedom in T, X and the bath). f (n*3) must hold F(x(t)) on entry and holds F at the end.
  *
  *  kind = ORA_NVE: velocity Verlet, order of Sec. "NVE molecular dynamics
  *    simulation": x += v dt + a dt^2/2; wrap; v += a dt/2; a = F(x)/m;
@@ -436,7 +445,7 @@ enum { ORA_NVE = 0, ORA_NOSE_HOOVER = 1, ORA_RESAMPLE = 2, ORA_NOSE_HOOVER_EXACT
  *    ora_maxwell_boltzmann at T_target with draw number step/nstep_boltz
  *    (Sec. "NVT molecular dynamics simulation").
  *  kind = ORA_NOSE_HOOVER(_EXACT): Fox-Andersen update of Appendix B, with
- *    X = 3n and g = (sum m v^2 - X T)/Q:
+ *    X = ndim n and g = (sum m v^2 - X T)/Q:
  *      x(t+dt)   = x + v dt + (F/m - xi v) dt^2/2          Eq. (Noseupdate_ri)
  *      ln s(t+dt)= ln s + xi dt + g dt^2/2                  Eq. (Noseupdate_lns)
  *      xi_a      = xi + g dt                                Eq. (Noseupdate_xiapprox)
@@ -449,22 +458,23 @@ enum { ORA_NVE = 0, ORA_NOSE_HOOVER = 1, ORA_RESAMPLE = 2, ORA_NOSE_HOOVER_EXACT
  *
  * Steps are numbered step0+1 .. step0+nsteps. Every log_every steps (if
  * log_every > 0) one ora_thermo record is written after the thermostat has
- * acted: T = sum m v^2 / (3n), PE/N, KE/N, Etot/N, W, and
+ * acted: T = sum m v^2 / (ndim n), PE/N, KE/N, Etot/N, W, and
  * H = KE + PE + Q xi^2/2 + X T ln s (Eq. (HNosetilde); NVE: H = Etot).
  */
-int ora_run(int64_t n, double *pos, double *vel, double *f, int32_t *img,
+int ora_run(int64_t n, int ndim, double *pos, double *vel, double *f, int32_t *img,
             const int32_t *types, int ntypes, const double *eps, const double *sig, const double *rc,
             double L, double mass, double dt, int64_t step0, int64_t nsteps,
             int kind, double T_target, double Q, int64_t nstep_boltz, uint64_t seed,
             double *state, double *thermo, int64_t log_every)
 {
     if (n < 1 || !pos || !vel || !f || !(dt > 0.0) || !(mass > 0.0) || nsteps < 0) return -1;
+    if (ndim != 2 && ndim != 3) return -1;
     if (kind < 0 || kind > 3) return -1;
     if ((kind == ORA_NOSE_HOOVER || kind == ORA_NOSE_HOOVER_EXACT) && (!(Q > 0.0) || !state)) return -1;
     if (kind == ORA_RESAMPLE && nstep_boltz < 1) return -1;
     int e = ora_check_tables(ntypes, eps, sig, rc, L);
     if (e) return e;
-    const double X = 3.0 * (double)n;
+    const double X = (double)ndim * (double)n;
     double *fn = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     if (!fn) return -5;
     double xi = state ? state[0] : 0.0, lns = state ? state[1] : 0.0;
@@ -512,7 +522,7 @@ int ora_run(int64_t n, double *pos, double *vel, double *f, int32_t *img,
             if (e) { free(fn); return e; }
             for (int64_t i = 0; i < 3 * n; ++i) vel[i] += 0.5 * (f[i] / mass) * dt;
             if (kind == ORA_RESAMPLE && step % nstep_boltz == 0) {
-                e = ora_maxwell_boltzmann(n, T_target, mass, seed, (uint64_t)(step / nstep_boltz), NULL, vel);
+                e = ora_maxwell_boltzmann(n, ndim, T_target, mass, seed, (uint64_t)(step / nstep_boltz), NULL, vel);
                 if (e) { free(fn); return e; }
             }
         }
@@ -546,11 +556,13 @@ int ora_run(int64_t n, double *pos, double *vel, double *f, int32_t *img,
  * Every pair j > i with r < rmax adds to bin floor(r/dr); like pairs count
  * twice (once per ordered pair), unlike pairs once. Normalisation divides by
  * the shell volume 4/3 pi ((k+1)^3 - k^3) dr^3 and by N_a(N_a - 1)/V
- * (like) or N_A N_B / V (unlike), V = L^3. g holds 3*nbins: AA, BB, AB. */
-int ora_rdf(int64_t n, const double *pos, const int32_t *types, double L, double dr, int64_t nbins,
+ * (like) or N_A N_B / V (unlike), V = L^3. ndim = 2 (the 2-D problem of Sec.
+ * "Suggested problems", which asks for the shell volume to be adjusted): the
+ * shell area pi ((k+1)^2 - k^2) dr^2 and V = L^2. g holds 3*nbins: AA, BB, AB. */
+int ora_rdf(int64_t n, int ndim, const double *pos, const int32_t *types, double L, double dr, int64_t nbins,
             double *g)
 {
-    if (n < 2 || !(dr > 0.0) || nbins < 1 || !g) return -1;
+    if (n < 2 || (ndim != 2 && ndim != 3) || !(dr > 0.0) || nbins < 1 || !g) return -1;
     double rmax = dr * (double)nbins;
     if (rmax > 0.5 * L * (1.0 + 1e-12)) return -2;
     int64_t na = 0, nb = 0;
@@ -570,9 +582,10 @@ int ora_rdf(int64_t n, const double *pos, const int32_t *types, double L, double
             else if (types[i] == 1 && types[j] == 1) h[nbins + k] += 2.0;
             else h[2 * nbins + k] += 1.0;
         }
-    double V = L * L * L;
+    double V = ndim == 3 ? L * L * L : L * L;
     for (int64_t k = 0; k < nbins; ++k) {
-        double shell = (4.0 / 3.0) * M_PI * (pow((double)(k + 1), 3) - pow((double)k, 3)) * dr * dr * dr;
+        double shell = ndim == 3 ? (4.0 / 3.0) * M_PI * (pow((double)(k + 1), 3) - pow((double)k, 3)) * dr * dr * dr
+                                 : M_PI * (pow((double)(k + 1), 2) - pow((double)k, 2)) * dr * dr;
         g[k] = (na > 1) ? h[k] / shell * V / ((double)na * (double)(na - 1)) : 0.0;
         g[nbins + k] = (nb > 1) ? h[nbins + k] / shell * V / ((double)nb * (double)(nb - 1)) : 0.0;
         g[2 * nbins + k] = (na > 0 && nb > 0) ? h[2 * nbins + k] / shell * V / ((double)na * (double)nb) : 0.0;

@@ -15,6 +15,7 @@
 struct md_system {
   // configuration
   int nrep = 0, ntypes = 0;
+  int ndim = 3;         // 2: particles in the plane z = L/2, v_z = 0 (two-dimensional model)
   int64_t n_total = 0;  // particles, caller order
   int64_t ntot = 0;     // slots (padded)
   int ntiles = 0;
@@ -170,10 +171,10 @@ void dfree(md_system* s, T*& p) {
 // ------------------------------------------------------------------ kernels
 
 // Map caller-order particle g to its slot: identity order inside a replica.
-__global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const RepDev* reps, const int32_t* rep_of,
-                            const uint8_t* typ_caller, const double* pos, const double* vel, int cur, uint64_t* pfx,
-                            uint4* pq, float* velf, float* frcf, uint4* xbq, double4_32a* p4, double* veld,
-                            double* frcd, double4_32a* xbd, int32_t* gid, uint8_t* typ, int32_t* img) {
+__global__ void k_set_state(bool mixed, int ndim, int64_t n_total, int64_t ntot, const RepDev* reps,
+                            const int32_t* rep_of, const uint8_t* typ_caller, const double* pos, const double* vel,
+                            int cur, uint64_t* pfx, uint4* pq, float* velf, float* frcf, uint4* xbq, double4_32a* p4,
+                            double* veld, double* frcd, double4_32a* xbd, int32_t* gid, uint8_t* typ, int32_t* img) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_total) return;
   const RepDev& R = reps[rep_of[g]];
@@ -181,13 +182,14 @@ __global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const Rep
   const uint32_t t = typ_caller[g];
   double x[3];
   for (int c = 0; c < 3; ++c) x[c] = kamd::wrap_box(pos[3 * g + c], R.L);
+  if (ndim == 2) x[2] = 0.5 * R.L;  // two dimensions: the plane z = L/2
   if (mixed) {
     uint32_t hi[3];
     for (int c = 0; c < 3; ++c) {
       const uint64_t u = kamd::to_fixed(x[c], R.invL);
       pfx[c * ntot + i] = u;
       hi[c] = (uint32_t)(u >> 32);
-      velf[c * ntot + i] = vel ? (float)vel[3 * g + c] : 0.0f;
+      velf[c * ntot + i] = (vel && (ndim == 3 || c < 2)) ? (float)vel[3 * g + c] : 0.0f;
       frcf[c * ntot + i] = 0.0f;
     }
     pq[i] = make_uint4(hi[0], hi[1], hi[2], t);
@@ -196,7 +198,7 @@ __global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const Rep
     p4[i] = make_double4_32a(x[0], x[1], x[2], (double)t);
     xbd[i] = p4[i];
     for (int c = 0; c < 3; ++c) {
-      veld[c * ntot + i] = vel ? vel[3 * g + c] : 0.0;
+      veld[c * ntot + i] = (vel && (ndim == 3 || c < 2)) ? vel[3 * g + c] : 0.0;
       frcd[c * ntot + i] = 0.0;
     }
   }
@@ -205,23 +207,25 @@ __global__ void k_set_state(bool mixed, int64_t n_total, int64_t ntot, const Rep
   typ[i] = (uint8_t)t;
 }
 
-// Simple-cubic lattice with jitter (Sec. "Initialization of positions").
-__global__ void k_lattice(int64_t n_total, const RepDev* reps, const int32_t* rep_of, double jitter, uint64_t seed,
-                          double* pos) {
+// Simple-cubic lattice with jitter (Sec. "Initialization of positions"); in
+// two dimensions a square lattice in the plane z = L/2.
+__global__ void k_lattice(int ndim, int64_t n_total, const RepDev* reps, const int32_t* rep_of, double jitter,
+                          uint64_t seed, double* pos) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_total) return;
   const RepDev& R = reps[rep_of[g]];
   const int64_t p = g - R.out0, n = R.n;
   int64_t m = 1;
-  while (m * m * m < n) ++m;
+  if (ndim == 3) while (m * m * m < n) ++m;
+  else while (m * m < n) ++m;
   const double a = R.L / (double)m;
-  const int64_t sites = m * m * m;
+  const int64_t sites = ndim == 3 ? m * m * m : m * m;
   const int64_t site = (int64_t)(((unsigned __int128)p * (unsigned __int128)sites) / (unsigned __int128)n);
   const int64_t k[3] = {site % m, (site / m) % m, site / (m * m)};
   double u[3];
   kamd::jitter3(seed, (uint32_t)p, u);
   for (int c = 0; c < 3; ++c) {
-    double x = (0.5 + (double)k[c]) * a + jitter * u[c];
+    double x = (ndim == 2 && c == 2) ? 0.5 * R.L : (0.5 + (double)k[c]) * a + jitter * u[c];
     if (x >= R.L) x -= R.L;
     else if (x < 0.0) x += R.L;
     pos[3 * g + c] = x;
@@ -430,38 +434,62 @@ __global__ void k_rdf(bool mixed, int64_t ntot, int nbins, double dr, double ski
   }
 }
 
-// Pairs inside their cutoff, counted from the full Verlet list (each pair twice).
-__global__ void k_count_pairs(bool mixed, int64_t ntot, int T, int maxrows, int ntypes, const RepDev* reps,
-                              const int32_t* tile_rep, int cur, const uint4* pq, const double4_32a* p4, const int32_t* nbr,
-                              const int32_t* nnb, const float* rc2f, const double* rc2d, unsigned long long* out) {
+// Pairs (i < j) inside their cutoff r < r_c,ab, from exact distances (mixed:
+// 64-bit fixed-point differences; FP64: the minimum-image branch rule), found
+// through the cells of the last list build. Every particle has moved less
+// than half the outer skin since, so the cells within (r_c,max + skin_outer)
+// of its current position hold every partner; a replica with too few cells
+// for that is scanned whole.
+__global__ void k_count_pairs(bool mixed, int64_t ntot, int ntypes, double reach, const RepDev* reps,
+                              const int32_t* tile_rep, const uint64_t* pfx, const double4_32a* p4, const uint8_t* typ,
+                              const int32_t* cstart, const double* rc2d, unsigned long long* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntot) return;
   const RepDev& R = reps[tile_rep[i >> 5]];
   if (i - R.off >= R.n) return;
-  const int gsz = 32 * T;
-  unsigned long long c = 0;
-  for (int s = 0; s < T; ++s) {
-    const int32_t* lb = nbr + list_col(i >> 5, maxrows, T, (int)(i & 31) * T + s);
-    const int cnt = nnb[i * T + s];
-    for (int q = 0; q < cnt; ++q) {
-      const int j = lb[list_at(0, q, gsz)];
-      if (mixed) {
-        const uint4 a = pq[i], b = pq[j];
-        const float dx = (float)(int)(a.x - b.x) * R.fxs, dy = (float)(int)(a.y - b.y) * R.fxs,
-                    dz = (float)(int)(a.z - b.z) * R.fxs;
-        c += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rc2f[a.w * ntypes + b.w];
-      } else {
-        const double4_32a a = p4[i], b = p4[j];
-        double d[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
-        for (int k = 0; k < 3; ++k) {
-          if (d[k] > 0.5 * R.L) d[k] -= R.L;
-          else if (d[k] < -0.5 * R.L) d[k] += R.L;
-        }
-        c += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2d[(int)a.w * ntypes + (int)b.w];
-      }
-    }
+  const int ti = typ[i];
+  double xi[3];
+  uint64_t ui[3];
+  for (int c = 0; c < 3; ++c) {
+    if (mixed) ui[c] = pfx[c * ntot + i];
+    else xi[c] = c == 0 ? p4[i].x : c == 1 ? p4[i].y : p4[i].z;
   }
-  if (c) atomicAdd(out, c);
+  unsigned long long cnt = 0;
+  auto visit = [&](int64_t j) {
+    if (j <= i) return;
+    double d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      double d;
+      if (mixed) {
+        d = (double)(int64_t)(ui[c] - pfx[c * ntot + j]) * (R.L * (1.0 / 18446744073709551616.0));
+      } else {
+        const double xj = c == 0 ? p4[j].x : c == 1 ? p4[j].y : p4[j].z;
+        d = xi[c] - xj;
+        if (d > 0.5 * R.L) d -= R.L;
+        else if (d < -0.5 * R.L) d += R.L;
+      }
+      d2 += d * d;
+    }
+    cnt += d2 < rc2d[ti * ntypes + typ[j]];
+  };
+  const int nc = R.nc;
+  const int layers = nc > 0 ? (int)ceil(reach * (1.0 + 1e-6) / (double)R.cellw) : 0;
+  if (nc == 0 || 2 * layers + 1 > nc) {
+    for (int64_t j = R.off; j < R.off + R.n; ++j) visit(j);
+  } else {
+    int cc[3];
+    for (int c = 0; c < 3; ++c) {
+      if (mixed) cc[c] = (int)(((uint64_t)(uint32_t)(ui[c] >> 32) * (uint64_t)nc) >> 32);
+      else cc[c] = min(max((int)(xi[c] * (double)nc * R.invL), 0), nc - 1);
+    }
+    for (int oz = -layers; oz <= layers; ++oz)
+      for (int oy = -layers; oy <= layers; ++oy)
+        for (int ox = -layers; ox <= layers; ++ox) {
+          const int c = (((cc[2] + oz + 8 * nc) % nc) * nc + (cc[1] + oy + 8 * nc) % nc) * nc + (cc[0] + ox + 8 * nc) % nc;
+          for (int j = cstart[R.cs0 + c]; j < cstart[R.cs0 + c + 1]; ++j) visit(j);
+        }
+  }
+  if (cnt) atomicAdd(out, cnt);
 }
 
 // Sum of n non-negative ints (warp sums, one atomic per warp).
@@ -526,10 +554,12 @@ int list_capacity(const md_system* s) {
   double dens = 0;
   int64_t nmax = 0;
   for (int r = 0; r < s->nrep; ++r) {
-    dens = std::max(dens, (double)s->n_per[r] / (s->L_per[r] * s->L_per[r] * s->L_per[r]));
+    const double Lr = s->L_per[r];
+    dens = std::max(dens, (double)s->n_per[r] / (s->ndim == 3 ? Lr * Lr * Lr : Lr * Lr));
     nmax = std::max(nmax, s->n_per[r]);
   }
-  double est = 4.0 / 3.0 * M_PI * rl * rl * rl * dens;
+  // particles within the list radius: a sphere, or in two dimensions a disc
+  double est = s->ndim == 3 ? 4.0 / 3.0 * M_PI * rl * rl * rl * dens : M_PI * rl * rl * dens;
   int cap = (int)std::ceil(1.5 * est + 32);
   // KAMD_LIST_CAPACITY: start from a given capacity (the list still grows on overflow)
   if (const char* e = std::getenv("KAMD_LIST_CAPACITY")) cap = std::max(1, std::atoi(e));
@@ -541,12 +571,13 @@ int list_capacity(const md_system* s) {
 // 1x1x1, 2x1x1, 2x2x1, 2x2x2) as keep the CTA's threads busy at T threads
 // per particle. KAMD_LIST_GROUP (1, 2, 4 or 8) overrides the choice.
 void choose_groups(md_system* s) {
-  double occ = 0.0;
+  double occ = 0.0;  // particles per occupied cell (two dimensions: only the cells of the plane hold particles)
   for (int r = 0; r < s->nrep; ++r) {
     const RepDev& R = s->reps[r];
     if (R.nc == 0) continue;
-    const double dens = (double)s->n_per[r] / (R.L * R.L * R.L);
-    occ = std::max(occ, dens * (double)R.cellw * R.cellw * R.cellw);
+    const double w = (double)R.cellw;
+    occ = std::max(occ, s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
+                                     : (double)s->n_per[r] / (R.L * R.L) * w * w);
   }
   int g = 1;
   if (occ > 0.0) {
@@ -559,6 +590,7 @@ void choose_groups(md_system* s) {
     const int v = std::atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) g = v;
   }
+  if (s->ndim == 2 && g > 4) g = 4;  // a plane: groups of 1, 2 or 2x2 cells
   s->gx = g >= 2 ? 2 : 1;
   s->gy = g >= 4 ? 2 : 1;
   s->gz = g >= 8 ? 2 : 1;
@@ -569,14 +601,17 @@ void choose_groups(md_system* s) {
 // with headroom over the mean (overflow regrows it).
 int stage_capacity(md_system* s) {
   choose_groups(s);
-  const double nu = (double)(s->gx + 2) * (s->gy + 2) * (s->gz + 2);
+  // occupied union cells (two dimensions: one plane of cells)
+  const double nu = s->ndim == 3 ? (double)(s->gx + 2) * (s->gy + 2) * (s->gz + 2) : (double)(s->gx + 2) * (s->gy + 2);
   int cap = 64;
   for (int r = 0; r < s->nrep; ++r) {
     const RepDev& R = s->reps[r];
-    const double dens = (double)s->n_per[r] / (R.L * R.L * R.L);
+    const double w = (double)R.cellw;
+    const double occ = s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
+                                    : (double)s->n_per[r] / (R.L * R.L) * w * w;
     int need;
     if (R.nc > 0) {
-      const double mean = nu * dens * (double)R.cellw * R.cellw * R.cellw;
+      const double mean = nu * occ;
       need = (int)std::ceil(1.1 * mean + 6.0 * std::sqrt(mean) + 32.0);
     } else {
       need = (int)s->n_per[r];
@@ -726,6 +761,7 @@ KParams make_params(const md_system* s) {
   std::memset(&p, 0, sizeof(p));
   p.nrep = s->nrep;
   p.ntypes = s->ntypes;
+  p.ndim = s->ndim;
   p.ntot = s->ntot;
   p.ntiles = s->ntiles;
   p.T = s->tun.threads_per_atom;
@@ -970,7 +1006,7 @@ md_status set_state_impl(md_system* s, const double* pos, const double* vel, int
   }
   const int b = 256;
   k_set_state<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(
-      s->mixed, s->n_total, s->ntot, s->d_reps, s->d_rep_of_caller, s->d_typ_caller, dpos, dvel, 0, s->d_pfx,
+      s->mixed, s->ndim, s->n_total, s->ntot, s->d_reps, s->d_rep_of_caller, s->d_typ_caller, dpos, dvel, 0, s->d_pfx,
       s->d_pq[0], s->d_velf, s->d_frcf, s->d_xbq, s->d_p4[0], s->d_veld, s->d_frcd, s->d_xbd, s->d_gid, s->d_typ,
       s->d_img);
   CK(cudaGetLastError());
@@ -1025,11 +1061,12 @@ void kamd_set_global_error(const std::string& msg) { g_create_err = msg; }
 
 extern "C" {
 
-md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, const uint8_t* types, int ntypes,
-                          const double* eps, const double* sigma, const double* rc, double mass, double skin,
-                          md_precision prec, void* stream, md_system** out) {
+md_status md_create_batch_dim(int ndim, int nrep, const int64_t* n_per, const double* L_per, const uint8_t* types,
+                              int ntypes, const double* eps, const double* sigma, const double* rc, double mass,
+                              double skin, md_precision prec, void* stream, md_system** out) {
   if (!out) return fail(nullptr, MD_ERR_INVALID_ARG, "out must not be NULL");
   *out = nullptr;
+  if (ndim != 2 && ndim != 3) return fail(nullptr, MD_ERR_INVALID_ARG, "ndim must be 2 or 3");
   if (nrep < 1 || !n_per || !L_per || !types) return fail(nullptr, MD_ERR_INVALID_ARG, "nrep >= 1 and arrays required");
   if (prec != MD_PREC_FP64 && prec != MD_PREC_MIXED) return fail(nullptr, MD_ERR_INVALID_ARG, "unknown precision");
   if (!(mass > 0)) return fail(nullptr, MD_ERR_INVALID_ARG, "mass must be > 0");
@@ -1048,6 +1085,7 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
     if (types[g] >= ntypes) return fail(nullptr, MD_ERR_INVALID_ARG, "type index out of range");
 
   md_system* s = new md_system();
+  s->ndim = ndim;
   s->stream = (cudaStream_t)stream;
   s->nrep = nrep;
   s->ntypes = ntypes;
@@ -1184,9 +1222,15 @@ md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, c
   return MD_OK;
 }
 
+md_status md_create_batch(int nrep, const int64_t* n_per, const double* L_per, const uint8_t* types, int ntypes,
+                          const double* eps, const double* sigma, const double* rc, double mass, double skin,
+                          md_precision prec, void* stream, md_system** out) {
+  return md_create_batch_dim(3, nrep, n_per, L_per, types, ntypes, eps, sigma, rc, mass, skin, prec, stream, out);
+}
+
 md_status md_create(int64_t n, const uint8_t* types, int ntypes, double L, const double* eps, const double* sigma,
                     const double* rc, double mass, double skin, md_precision prec, void* stream, md_system** out) {
-  return md_create_batch(1, &n, &L, types, ntypes, eps, sigma, rc, mass, skin, prec, stream, out);
+  return md_create_batch_dim(3, 1, &n, &L, types, ntypes, eps, sigma, rc, mass, skin, prec, stream, out);
 }
 
 md_status md_set_state(md_system* s, const double* pos, const double* vel, int on_device) {
@@ -1224,8 +1268,8 @@ md_status md_init_lattice(md_system* s, const double* T0, double jitter, uint64_
   for (int r = 0; r < s->nrep; ++r)
     if (!(T0[r] >= 0)) return fail(s, MD_ERR_INVALID_ARG, "T0 must be >= 0");
   const int b = 256;
-  k_lattice<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(s->n_total, s->d_reps, s->d_rep_of_caller, jitter, seed,
-                                                            s->d_io);
+  k_lattice<<<blocks_for(s->n_total, b), b, 0, s->stream>>>(s->ndim, s->n_total, s->d_reps, s->d_rep_of_caller,
+                                                            jitter, seed, s->d_io);
   CK(cudaGetLastError());
   CKS(set_state_impl(s, s->d_io, nullptr, 1));
   CKS(download_reps(s));
@@ -1302,7 +1346,7 @@ md_status md_step_nvt(md_system* s, double dt, int64_t nsteps, const double* T_t
   for (int r = 0; r < s->nrep; ++r) {
     RepDev& R = s->reps[r];
     R.T_target = T_target[r];
-    if (k != MD_KIND_RESAMPLE) R.Q = 3.0 * R.n * T_target[r] * param * param;
+    if (k != MD_KIND_RESAMPLE) R.Q = (double)s->ndim * R.n * T_target[r] * param * param;
   }
   CKS(upload_reps(s));
   return step_common(s, k, dt, nsteps, nb, seed, log, log_every);
@@ -1342,9 +1386,13 @@ md_status md_rdf(md_system* s, double dr, int64_t nbins, double* g, int reset) {
     for (int r = 0; r < s->nrep; ++r) {
       int64_t na = 0, nb = 0;
       for (int64_t q = 0; q < s->n_per[r]; ++q) (types[s->out0[r] + q] == 0 ? na : nb) += 1;
-      const double V = s->L_per[r] * s->L_per[r] * s->L_per[r];
+      // V and the shell volume of bin k; in two dimensions the area L^2 and the ring pi((k+1)^2 - k^2)dr^2
+      const double Lr = s->L_per[r];
+      const double V = s->ndim == 3 ? Lr * Lr * Lr : Lr * Lr;
       for (int64_t k = 0; k < nbins; ++k) {
-        const double shell = 4.0 / 3.0 * M_PI * (std::pow((double)(k + 1), 3) - std::pow((double)k, 3)) * dr * dr * dr;
+        const double shell =
+            s->ndim == 3 ? 4.0 / 3.0 * M_PI * (std::pow((double)(k + 1), 3) - std::pow((double)k, 3)) * dr * dr * dr
+                         : M_PI * (std::pow((double)(k + 1), 2) - std::pow((double)k, 2)) * dr * dr;
         const unsigned long long* hr = h.data() + (size_t)r * 3 * nbins;
         const double m = (double)s->rdf_meas * s->nrep;
         if (na > 1) g[k] += hr[k] / shell * V / ((double)na * (na - 1)) / m;
@@ -1557,25 +1605,19 @@ md_status md_count_pairs(md_system* s, int64_t* pairs) {
   CKS(download_ctl(s));
   if (s->ctl.pending & MD_FLAG_REBUILD) CKS(run_op(s, MD_OP_REBUILD, MD_KIND_NVE, 0, 0, 0, 0, 0, 0, nullptr));
   CKS(download_ctl(s));
-  KParams p = make_params(s);
-  float rc2f[16];
   double rc2d[16];
-  for (int t = 0; t < 16; ++t) {
-    rc2f[t] = p.tab_f[t][0];
-    rc2d[t] = p.tab_d[t][0];
-  }
-  CK(cudaMemcpyAsync(s->d_io, rc2d, sizeof rc2d, cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->d_io + 16, rc2f, sizeof rc2f, cudaMemcpyHostToDevice, s->stream));
+  for (int t = 0; t < s->ntypes * s->ntypes; ++t) rc2d[t] = s->rc[t] * s->rc[t];
+  CK(cudaMemcpyAsync(s->d_io, rc2d, sizeof(double) * s->ntypes * s->ntypes, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemsetAsync(s->d_count, 0, 8, s->stream));
-  const int b = 256;
+  const int b = 128;
   k_count_pairs<<<blocks_for(s->ntot, b), b, 0, s->stream>>>(
-      s->mixed, s->ntot, s->tun.threads_per_atom, s->maxrows, s->ntypes, s->d_reps, s->d_tile_rep, s->ctl.cur,
-      s->d_pq[s->ctl.cur], s->d_p4[s->ctl.cur], s->d_nbr, s->d_nnb, (const float*)(s->d_io + 16), s->d_io, s->d_count);
+      s->mixed, s->ntot, s->ntypes, rc_max(s) + s->tun.skin_outer, s->d_reps, s->d_tile_rep, s->d_pfx,
+      s->d_p4[s->ctl.cur], s->d_typ, s->d_cstart, s->d_io, s->d_count);
   CK(cudaGetLastError());
   unsigned long long c = 0;
   CK(cudaMemcpyAsync(&c, s->d_count, 8, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  *pairs = (int64_t)(c / 2);
+  *pairs = (int64_t)c;
   return MD_OK;
 }
 

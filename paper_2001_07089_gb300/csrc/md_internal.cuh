@@ -120,6 +120,7 @@ struct KParams {
   // sizes
   int nrep;
   int ntypes;
+  int ndim;            // 3, or 2: every particle in the plane z = L/2 with v_z = 0
   int64_t ntot;        // slots
   int ntiles;
   int T;               // lanes per particle

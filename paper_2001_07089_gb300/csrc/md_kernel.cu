@@ -403,7 +403,6 @@ __device__ void force_phase(const KParams& p, Shared& sh, int cur, int kick, boo
   const int lane = threadIdx.x & 31;
   const int nunits = p.ntiles * T;
   const int64_t nt = p.ntot;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   int64_t ub, ue, us;
   sm_share(sh, nunits, (int)(blockDim.x >> 5), (int)(threadIdx.x >> 5), &ub, &ue, &us);
   for (int u = (int)ub; u < ue; u += (int)us) {
@@ -686,6 +685,7 @@ __device__ void resample_draw_phase(const KParams& p, uint64_t draw, double* par
     const bool act = i - R.off < R.n;
     double g[3] = {0, 0, 0};
     if (act) gauss3(p.seed, draw, (uint32_t)(p.gid[i] - R.out0), g);
+    if (p.ndim == 2) g[2] = 0.0;  // particles stay in their plane: v_z = 0
     if constexpr (MIX) {
       float e[4] = {0.f, 0.f, 0.f, 0.f};
       if (act) {
@@ -832,7 +832,7 @@ __device__ bool reduce_phase(const KParams& p, Shared& sh, const double* part, i
 
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh) {
-  const double n = (double)R.n, X = 3.0 * n, dt = p.dt;
+  const double n = (double)R.n, X = (double)p.ndim * n, dt = p.dt;
   if (mode == RED_RESAMPLE) {
     const double mx = acc[0] / n, my = acc[1] / n, mz = acc[2] / n;
     const double S = acc[3] - n * (mx * mx + my * my + mz * mz);

@@ -31,7 +31,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
                          ("ke_per_n", np.float64), ("etot_per_n", np.float64), ("virial", np.float64),
                          ("h_nh", np.float64), ("xi", np.float64)])
 
-EXPORTED = ("md_create", "md_create_batch", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
+EXPORTED = ("md_create", "md_create_batch", "md_create_batch_dim", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_msd_tw", "md_set_tuning", "md_get_tuning", "md_autotune",
             "md_autotune_skin",
             "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_forces_noalloc", "md_last_error",
@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
         sig = {
             "md_create": [i64, P, c_int, dbl, P, P, P, dbl, dbl, c_int, P, ctypes.POINTER(P)],
             "md_create_batch": [c_int, P, P, P, c_int, P, P, P, dbl, dbl, c_int, P, ctypes.POINTER(P)],
+            "md_create_batch_dim": [c_int, c_int, P, P, P, c_int, P, P, P, dbl, dbl, c_int, P, ctypes.POINTER(P)],
             "md_set_state": [P, P, P, c_int],
             "md_get_state": [P, P, P, P, c_int],
             "md_init_lattice": [P, P, dbl, u64],
@@ -156,6 +157,18 @@ def md_create_batch(n_per, L_per, types, ntypes, eps, sigma, rc, mass, skin, pre
     _check(load().md_create_batch(len(n), n.ctypes.data, Lp.ctypes.data, t.ctypes.data, int(ntypes), e.ctypes.data,
                                   s.ctypes.data, r.ctypes.data, float(mass), float(skin), int(prec), stream,
                                   ctypes.byref(h)))
+    return h
+
+
+def md_create_batch_dim(ndim, n_per, L_per, types, ntypes, eps, sigma, rc, mass, skin, prec, stream=None):
+    n = np.ascontiguousarray(n_per, dtype=np.int64)
+    Lp = _f64(L_per)
+    t = np.ascontiguousarray(types, dtype=np.uint8)
+    e, s, r = _f64(eps), _f64(sigma), _f64(rc)
+    h = ctypes.c_void_p()
+    _check(load().md_create_batch_dim(int(ndim), len(n), n.ctypes.data, Lp.ctypes.data, t.ctypes.data, int(ntypes),
+                                      e.ctypes.data, s.ctypes.data, r.ctypes.data, float(mass), float(skin), int(prec),
+                                      stream, ctypes.byref(h)))
     return h
 
 
@@ -271,14 +284,21 @@ def md_destroy(h):
 # ---------------------------------------------------------------- convenience
 
 class System:
-    """One system (or a batch of replicas when ``n`` is a sequence)."""
+    """One system (or a batch of replicas when ``n`` is a sequence); ``ndim=2`` for the
+    two-dimensional model (particles in the plane z = L/2)."""
 
-    def __init__(self, n, L, types, eps, sigma, rc, mass=1.0, skin=0.3, precision="mixed", stream=None):
+    def __init__(self, n, L, types, eps, sigma, rc, mass=1.0, skin=0.3, precision="mixed", stream=None, ndim=3):
         prec = MD_PREC_MIXED if precision == "mixed" else MD_PREC_FP64
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.ntypes = int(np.asarray(eps).shape[0])
-        if np.ndim(n) == 0:
+        self.ndim = int(ndim)
+        if self.ndim != 3:
+            self.n_per = np.atleast_1d(np.asarray(n, dtype=np.int64))
+            self.L_per = np.broadcast_to(np.asarray(L, dtype=np.float64), self.n_per.shape).copy()
+            self._h = md_create_batch_dim(self.ndim, self.n_per, self.L_per, types, self.ntypes, eps, sigma, rc, mass,
+                                          skin, prec, stream)
+        elif np.ndim(n) == 0:
             self.n_per = np.array([int(n)], dtype=np.int64)
             self.L_per = np.array([float(L)])
             self._h = md_create(int(n), types, self.ntypes, float(L), eps, sigma, rc, mass, skin, prec, stream)

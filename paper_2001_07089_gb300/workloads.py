@@ -15,6 +15,8 @@ Sources of the numbers:
   B with an A (Sec. "Initialization of positions").
 * Density 1.2 and the workload sizes are those of the benchmark
   configurations (N = 1000, 32 000, 10^6, 8*10^6, and a 512-replica mix).
+* The two-dimensional variant (Sec. "Suggested problems"): N = 1000 at
+  N/L^2 = 1.204 (L = 28.82) with A:B = 65:35.
 """
 from __future__ import annotations
 
@@ -27,6 +29,9 @@ KA_SIG = np.array([[1.0, 0.8], [0.8, 0.88]])
 KA_RC = 2.5 * KA_SIG
 KA_MASS = 1.0
 DENSITY = 1.2
+# the two-dimensional problem (Sec. "Suggested problems"): N/L^2 = 1.204, A:B = 65:35
+DENSITY_2D = 1.204
+FRAC_B_2D = 0.35
 SKIN = 0.3
 DT = 0.005
 
@@ -34,6 +39,11 @@ DT = 0.005
 def box_length(n: int, density: float = DENSITY) -> float:
     """Edge of the cubic box holding n particles at the given number density."""
     return float((n / density) ** (1.0 / 3.0))
+
+
+def box_length_2d(n: int, density: float = DENSITY_2D) -> float:
+    """Edge of the square box holding n particles at the given areal density (two dimensions)."""
+    return float(np.sqrt(n / density))
 
 
 def ka_types(n: int, seed: int, frac_b: float = 0.2) -> np.ndarray:

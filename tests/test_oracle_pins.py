@@ -493,3 +493,105 @@ def test_threaded_force_sum_reproducible_and_equal_to_serial():
     scale = np.maximum(np.abs(serial["thermo"]), 1.0)
     assert np.max(np.abs(par["thermo"] - serial["thermo"]) / scale) < 1e-12
     assert np.array_equal(again["thermo"], serial["thermo"])
+
+
+# ------------------------------------------------------------- two dimensions
+# The 2-D Kob-Andersen problem of Sec. "Suggested problems": N = 1000 in a
+# square box at N/L^2 = 1.204 (L = 28.82), A:B = 65:35, 2 instead of 3 in
+# Eq. (equip3N), and the shell volume of g(r) adjusted to two dimensions.
+
+def test_2d_maxwell_boltzmann_exact_temperature_in_plane():
+    n, T = 1000, 0.4
+    v = oracle.maxwell_boltzmann(n, T, seed=5, draw=0, ndim=2)
+    assert np.all(v[:, 2] == 0.0)
+    assert np.all(np.abs(v.sum(axis=0)) < 1e-12)
+    assert np.sum(v * v) / (2 * n) == pytest.approx(T, rel=1e-13)
+    # x and y are the three-dimensional draws (same Philox stream), recentred and rescaled
+    v3 = np.array([oracle.gauss3(5, 0, p) for p in range(n)])[:, :2]
+    v3 -= v3.mean(axis=0)
+    v3 *= np.sqrt(2 * n * T / np.sum(v3 * v3))
+    assert np.allclose(v[:, :2], v3, rtol=1e-12, atol=1e-14)
+
+
+def test_2d_lattice_start_square_sites_in_one_plane():
+    n, L = 1000, wl.box_length_2d(1000)
+    assert L == pytest.approx(28.82, abs=5e-3)
+    pos, vel = oracle.init_lattice(n, L, 0.4, seed=3, jitter=0.0, ndim=2)
+    assert np.all(pos[:, 2] == 0.5 * L)
+    a = L / 32
+    k = np.rint(pos[:, :2] / a - 0.5).astype(int)
+    assert len({tuple(r) for r in k}) == n and k.min() == 0 and k.max() == 31
+    assert np.allclose(pos[:, :2], (k + 0.5) * a, atol=1e-12)
+    assert np.sum(vel * vel) / (2 * n) == pytest.approx(0.4, rel=1e-13)
+
+
+def test_2d_square_lattice_zero_force_and_lattice_sum():
+    """A perfect square A lattice at density 1.204: F_i = 0 by symmetry, F_z = 0, and V/N is half
+    the brute-force sum over the 2-D integer vectors inside the cutoff."""
+    m = 16
+    L = np.sqrt(m * m / 1.204)
+    a = L / m
+    k = np.arange(m)
+    gx, gy = np.meshgrid(k, k, indexing="ij")
+    pos = np.stack([(gx.ravel() + 0.5) * a, (gy.ravel() + 0.5) * a, np.full(m * m, 0.5 * L)], axis=1)
+    types = np.zeros(m * m, dtype=np.int32)
+    f, v, w = oracle.forces(pos, types, ka_params(), L)
+    assert np.max(np.abs(f)) < 1e-11
+    vc = 4.0 * (2.5 ** -12 - 2.5 ** -6)
+    vsum = 0.0
+    for nx in range(-3, 4):
+        for ny in range(-3, 4):
+            if nx == ny == 0:
+                continue
+            r = a * np.hypot(nx, ny)
+            if r < 2.5:
+                vsum += 4.0 * (r ** -12 - r ** -6) - vc
+    assert v / (m * m) == pytest.approx(0.5 * vsum, rel=1e-12)
+
+
+def test_2d_ideal_gas_rdf_is_one_with_shell_areas():
+    n, L = 4000, 40.0
+    rng = np.random.default_rng(11)
+    pos = np.zeros((n, 3))
+    pos[:, :2] = rng.uniform(0, L, size=(n, 2))
+    pos[:, 2] = 0.5 * L
+    types = wl.ka_types(n, 11, frac_b=0.35).astype(np.int32)
+    g = oracle.rdf(pos, types, L, 0.5, 30, ndim=2)
+    for row in g:
+        assert abs(row[6:].mean() - 1.0) < 0.05
+    # the 3-D normalisation is not flat for a planar gas (it falls off like L / r)
+    g3 = oracle.rdf(pos, types, L, 0.5, 30, ndim=3)
+    assert g3[0, 6] > 1.8 * g3[0, 29] > 1.8
+
+
+def test_2d_nve_stays_in_plane_and_conserves_energy():
+    """2-D NVE from the melted square lattice: z and v_z stay exactly fixed, momentum stays zero,
+    the energy is conserved, and T = sum m v^2 / (2N)."""
+    n = 256
+    L = wl.box_length_2d(n)
+    types = wl.ka_types(n, 14, frac_b=0.35).astype(np.int32)
+    pos, vel = oracle.init_lattice(n, L, 1.0, seed=14, ndim=2)
+    melt = oracle.run(pos, vel, types, ka_params(), L, 0.005, 200, kind=oracle.RESAMPLE, T_target=1.0,
+                      nstep_boltz=10, seed=14, log_every=0, ndim=2)
+    out = oracle.run(melt["pos"], melt["vel"], types, ka_params(), L, 0.005, 1000, log_every=10, ndim=2)
+    assert np.all(out["pos"][:, 2] == 0.5 * L) and np.all(out["vel"][:, 2] == 0.0)
+    assert np.all(np.abs(out["vel"].sum(axis=0)) < 1e-10)
+    e = out["thermo"][:, 4]
+    assert np.ptp(e) < 5e-3
+    th = out["thermo"][-1]
+    assert th[1] == pytest.approx(np.sum(out["vel"] ** 2) / (2 * n), rel=1e-12)
+    # the resampling bath sets T exactly with 2N degrees of freedom
+    assert abs(np.sum(melt["vel"] ** 2) / (2 * n) - 1.0) < 1e-12
+
+
+def test_2d_nose_hoover_reaches_target_with_2n_degrees_of_freedom():
+    n = 256
+    L = wl.box_length_2d(n)
+    types = wl.ka_types(n, 15, frac_b=0.35).astype(np.int32)
+    pos, vel = oracle.init_lattice(n, L, 1.0, seed=15, ndim=2)
+    T = 0.45
+    out = oracle.run(pos, vel, types, ka_params(), L, 0.005, 6000, kind=oracle.NOSE_HOOVER, T_target=T,
+                     Q=2 * n * T * 0.5 ** 2, log_every=10, ndim=2)
+    assert abs(out["thermo"][300:, 1].mean() - T) < 0.04
+    h = out["thermo"][:, 6] / n
+    assert np.ptp(h[100:]) < 0.05 * np.ptp(out["thermo"][:, 4])
