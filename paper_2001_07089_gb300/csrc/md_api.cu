@@ -531,16 +531,28 @@ double rc_max(const md_system* s) {
 }
 
 // Cells per edge and list capacity follow from the skin; both are recomputed
-// whenever the tuning changes.
+// whenever the tuning changes. Cells are at least half the outer list radius
+// wide, so the list build scans the 5 x 5 x 5 cells around a particle's own
+// (less volume than 27 cells of the full radius, and the corners are culled);
+// a box with fewer than 5 such cells per edge uses cells of the full radius
+// (3 x 3 x 3), and one with fewer than 3 of those an all-pairs scan.
+// KAMD_CELL_REACH=1 keeps cells of the full radius (for tests of that path).
 void layout_cells(md_system* s) {
   const double rl = rc_max(s) + s->tun.skin_outer;
+  int reach = 2;
+  if (const char* e = std::getenv("KAMD_CELL_REACH")) reach = std::atoi(e) == 1 ? 1 : 2;
   int64_t cell0 = 0;
   for (int r = 0; r < s->nrep; ++r) {
     RepDev& R = s->reps[r];
-    int nc = (int)std::floor(R.L / rl);
+    int nr = reach;
+    int nc = (int)std::min(std::floor(R.L / (rl / nr)), 1024.0);
+    if (nr == 2 && nc < 5) {
+      nr = 1;
+      nc = (int)std::floor(R.L / rl);
+    }
     if (nc < 3) nc = 0;
-    if (nc > 1024) nc = 1024;
     R.nc = nc;
+    R.nr = nc > 0 ? nr : 1;
     R.cellw = nc > 0 ? (float)(R.L / nc) : 0.0f;
     R.cell0 = cell0;
     R.cs0 = cell0 + r;
@@ -579,21 +591,29 @@ void choose_groups(md_system* s) {
     occ = std::max(occ, s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
                                      : (double)s->n_per[r] / (R.L * R.L) * w * w);
   }
+  // cells per group: a power of two up to 4 x 4 x 4 (4 x 4 in a plane)
+  const int gmax = s->ndim == 3 ? 64 : 16;
   int g = 1;
   if (occ > 0.0) {
     // 10 % headroom: a group whose particles overflow the CTA needs a second,
     // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2)
     const double fit = 0.9 * (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
-    g = fit >= 8.0 ? 8 : (fit >= 4.0 ? 4 : (fit >= 2.0 ? 2 : 1));
+    while (2 * g <= gmax && 2 * g <= fit) g *= 2;
   }
   if (const char* e = std::getenv("KAMD_LIST_GROUP")) {
     const int v = std::atoi(e);
-    if (v == 1 || v == 2 || v == 4 || v == 8) g = v;
+    if (v >= 1 && v <= gmax && (v & (v - 1)) == 0) g = v;
   }
-  if (s->ndim == 2 && g > 4) g = 4;  // a plane: groups of 1, 2 or 2x2 cells
-  s->gx = g >= 2 ? 2 : 1;
-  s->gy = g >= 4 ? 2 : 1;
-  s->gz = g >= 8 ? 2 : 1;
+  // x doubles first, then y, then z (a plane: x and y only)
+  int gx = 1, gy = 1, gz = 1;
+  for (int k = 1; k < g; k *= 2) {
+    if (gx <= gy && (s->ndim == 2 || gx <= gz) && gx < 4) gx *= 2;
+    else if (gy <= gz || s->ndim == 2) gy *= 2;
+    else gz *= 2;
+  }
+  s->gx = gx;
+  s->gy = gy;
+  s->gz = gz;
 }
 
 // Staging area of the list build: the candidates of the cells around one
@@ -601,11 +621,12 @@ void choose_groups(md_system* s) {
 // with headroom over the mean (overflow regrows it).
 int stage_capacity(md_system* s) {
   choose_groups(s);
-  // occupied union cells (two dimensions: one plane of cells)
-  const double nu = s->ndim == 3 ? (double)(s->gx + 2) * (s->gy + 2) * (s->gz + 2) : (double)(s->gx + 2) * (s->gy + 2);
   int cap = 64;
   for (int r = 0; r < s->nrep; ++r) {
     const RepDev& R = s->reps[r];
+    // occupied union cells (two dimensions: one plane of cells)
+    const int e = 2 * R.nr;
+    const double nu = s->ndim == 3 ? (double)(s->gx + e) * (s->gy + e) * (s->gz + e) : (double)(s->gx + e) * (s->gy + e);
     const double w = (double)R.cellw;
     const double occ = s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
                                     : (double)s->n_per[r] / (R.L * R.L) * w * w;

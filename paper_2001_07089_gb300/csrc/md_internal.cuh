@@ -29,8 +29,8 @@
 #define MD_TILE 32
 #define MD_MAXTYPES 4
 #define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
-#define MD_UNION_MAX 64     // staged cells of one list-build group: (GX+2)(GY+2)(GZ+2) <= 4*4*4
-#define MD_ROWS_MAX 4       // (y, z) rows of cells in one list-build group: GY*GZ <= 4
+#define MD_UNION_MAX 512    // staged cells of one list-build group: (GX+2nr)(GY+2nr)(GZ+2nr) <= 8*8*8
+#define MD_ROWS_MAX 16      // (y, z) rows of cells in one list-build group: GY*GZ <= 4*4
 #define MD_RED_TILES 256    // tiles per chunk of the two-level per-replica reduction (default)
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
 
@@ -54,6 +54,7 @@ struct RepDev {
   int32_t ntiles;   // slots / 32
   int32_t tile0;    // first tile
   int32_t nc;       // cells per edge (0: list built by an all-pairs scan)
+  int32_t nr;       // cells on each side that the list build scans: 2 (cells >= r_list / 2 wide) or 1
   double L, invL;
   double fx64;      // 2^64 / L
   float Lf, fxs;    // L, L / 2^32
@@ -125,7 +126,7 @@ struct KParams {
   int ntiles;
   int T;               // lanes per particle
   int maxrows;         // list entries per column (capacity per particle = maxrows*T), a multiple of 4
-  int gx, gy, gz;      // cells per list-build group along x, y, z (1 or 2 each)
+  int gx, gy, gz;      // cells per list-build group along x, y, z (1, 2 or 4 each)
   int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps

@@ -983,19 +983,29 @@ __device__ __forceinline__ int scan_run_mix(uint32_t st_s, uint32_t rl2_s, int q
   return k;
 }
 
+// Distance from a particle at fraction f of its cell's width (f in [0, w)) to
+// the nearest face of the cell o cells away along one axis (0 for its own).
+__device__ __forceinline__ float face_dist(int o, float f, float w) {
+  return o < 0 ? f + (float)(-o - 1) * w : (o > 0 ? (w - f) + (float)(o - 1) * w : 0.0f);
+}
+
 // B6: Verlet lists, radius r_c,ab + skin, built per GROUP of up to GX x GY x
-// GZ neighbouring cells (one CTA per group). The union of the cells around
-// the group, (GX+2) x (GY+2) x (GZ+2) cells with x fastest, is staged in
-// shared memory once; each particle of the group then scans the 9 rows of 3
-// staged cells that make up its own 27-cell neighbourhood, list column s
-// taking the entries s, s + T, s + 2T, ... of every row. A replica too small
-// for a 3x3x3 cell grid is one group whose single staged "cell" is the whole
-// replica.
+// GZ neighbouring cells (one CTA per group). Cells are at least r_list / nr
+// wide (nr = 2: half-width cells, or nr = 1), so every partner of a particle
+// lies in the (2 nr + 1)^3 cells around its own. The union of the cells
+// around the group, (GX + 2nr) x (GY + 2nr) x (GZ + 2nr) cells with x fastest,
+// is staged in shared memory once; each particle of the group then scans the
+// (2 nr + 1)^2 rows of its own neighbourhood, each a run of (2 nr + 1)
+// consecutive staged cells, leaving out rows, and cells at the ends of rows,
+// that lie wholly beyond its largest list radius (with half-width cells that
+// skips the corners of the 5 x 5 x 5 block, so far fewer candidates are tested
+// than in 27 cells of full width). List column s takes the run entries s,
+// s + T, s + 2T, ... of every row. A replica too small for cells is one group
+// whose single staged "cell" is the whole replica.
 template <bool MIX>
 __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cur) {
   const int T = p.T, gsz = 32 * T;
   const int GX = p.gx, GY = p.gy, GZ = p.gz;
-  const int UX = GX + 2, UY = GY + 2, UZ = GZ + 2;
   extern __shared__ __align__(32) unsigned char dyn[];
   const int stage_cap = p.stage_cap;
   double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);  // FP64: positions, then slots
@@ -1003,9 +1013,9 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
   float4* st_f = reinterpret_cast<float4*>(dyn);
   uint4* st_u = reinterpret_cast<uint4*>(dyn);
   // union cells: first slot, staged base; group rows (ly, lz): first slot,
-  // particle count prefix, slot where the row's second x cell starts
+  // particle count prefix
   __shared__ int s_ulo[MD_UNION_MAX], s_ub[MD_UNION_MAX + 1];
-  __shared__ int s_plo[MD_ROWS_MAX], s_pb[MD_ROWS_MAX + 1], s_px1[MD_ROWS_MAX];
+  __shared__ int s_plo[MD_ROWS_MAX], s_pb[MD_ROWS_MAX + 1];
   __shared__ int s_ref;
   // groups, then one pseudo-group per all-pairs replica; grid-strided, so
   // that a rebuild of a few replicas still spreads over every SM
@@ -1023,32 +1033,35 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
     if (!R.doing_rebuild) continue;
     if (g >= p.ngroups && R.nc != 0) continue;
     const int nc = R.nc;
-    int nu, nrows;
+    const int nr = R.nr;  // cells of the stencil on each side
+    const int UX = GX + 2 * nr, UY = GY + 2 * nr, UZ = GZ + 2 * nr;
+    int nu, nrows, cx = 0, cy = 0, cz = 0;
     if (nc > 0) {
       const int ngx = (nc + GX - 1) / GX, ngy = (nc + GY - 1) / GY;
-      const int cx = (lg % ngx) * GX, cy = ((lg / ngx) % ngy) * GY, cz = (lg / (ngx * ngy)) * GZ;
+      cx = (lg % ngx) * GX;
+      cy = ((lg / ngx) % ngy) * GY;
+      cz = (lg / (ngx * ngy)) * GZ;
       const int gxe = min(GX, nc - cx), gye = min(GY, nc - cy), gze = min(GZ, nc - cz);
       nu = UX * UY * UZ;
       nrows = GY * GZ;
       for (int t = threadIdx.x; t < nu; t += blockDim.x) {
         const int ux = t % UX, uy = (t / UX) % UY, uz = t / (UX * UY);
-        const int q = (((cz - 1 + uz + nc) % nc) * nc + (cy - 1 + uy + nc) % nc) * nc + (cx - 1 + ux + nc) % nc;
+        const int q = (((cz - nr + uz + 4 * nc) % nc) * nc + (cy - nr + uy + 4 * nc) % nc) * nc +
+                      (cx - nr + ux + 4 * nc) % nc;
         const int lo = p.cstart[R.cs0 + q];
         s_ulo[t] = lo;
         s_ub[t] = p.cstart[R.cs0 + q + 1] - lo;  // count for now, prefix below
       }
       for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
         const int ly = t % GY, lz = t / GY;
-        int lo = 0, n = 0, x1 = 0;
+        int lo = 0, n = 0;
         if (ly < gye && lz < gze) {
           const int c0 = ((cz + lz) * nc + (cy + ly)) * nc + cx;  // cells cx .. cx+gxe-1 are consecutive
           lo = p.cstart[R.cs0 + c0];
           n = p.cstart[R.cs0 + c0 + gxe] - lo;
-          x1 = gxe > 1 ? p.cstart[R.cs0 + c0 + 1] : lo + n;
         }
         s_plo[t] = lo;
         s_pb[t] = n;
-        s_px1[t] = x1;
       }
     } else {
       nu = 1;
@@ -1058,24 +1071,29 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         s_ub[0] = R.n;
         s_plo[0] = (int)R.off;
         s_pb[0] = R.n;
-        s_px1[0] = (int)(R.off + R.n);
       }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-      // exclusive prefix of the staged-cell counts (nu <= 64: two per lane)
+      // exclusive prefix of the staged-cell counts: lane l sums its chunk of
+      // per consecutive counts (nu <= 32 * per), a warp scan, then the chunk
       const int lane = threadIdx.x;
-      const int c0 = 2 * lane < nu ? s_ub[2 * lane] : 0;
-      const int c1 = 2 * lane + 1 < nu ? s_ub[2 * lane + 1] : 0;
-      int incl = c0 + c1;
+      const int per = (nu + 31) / 32;
+      const int b0 = min(lane * per, nu), b1 = min(b0 + per, nu);
+      int sum = 0;
+      for (int t = b0; t < b1; ++t) sum += s_ub[t];
+      int incl = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
-      const int excl = incl - c0 - c1;
-      if (2 * lane < nu) s_ub[2 * lane] = excl;
-      if (2 * lane + 1 < nu) s_ub[2 * lane + 1] = excl + c0;
+      int run = incl - sum;
+      for (int t = b0; t < b1; ++t) {
+        const int c = s_ub[t];
+        s_ub[t] = run;
+        run += c;
+      }
       if (lane == 31) s_ub[nu] = incl;
       if (lane == 0) {
         int m = 0, ref = -1;
@@ -1101,12 +1119,13 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
     }
     // mixed path with enough cells per edge: stage coordinates relative to a
     // particle of the group as FP32 (exact integer differences, converted once
-    // per candidate). Every staged candidate then lies within (G + 1) cells of
-    // the reference along each axis, less than half the box, so differences
-    // of relative coordinates are the minimum image; the list test has a whole
-    // skin of margin, so FP32 is ample. Otherwise the fixed-point words are
-    // staged and every test takes the exact integer difference.
-    const bool rel = MIX && nc >= 2 * GX + 3 && nc >= 2 * GY + 3 && nc >= 2 * GZ + 3;
+    // per candidate). Every staged candidate then lies within (G + nr) cells
+    // of the reference along each axis, less than half the box, so
+    // differences of relative coordinates are the minimum image; the list
+    // test has a whole skin of margin, so FP32 is ample. Otherwise the
+    // fixed-point words are staged and every test takes the exact integer
+    // difference.
+    const bool rel = MIX && nc >= 2 * (GX + nr) + 1 && nc >= 2 * (GY + nr) + 1 && nc >= 2 * (GZ + nr) + 1;
     uint4 ref = make_uint4(0u, 0u, 0u, 0u);
     if constexpr (MIX) ref = p.pq[cur][s_ref];
     {
@@ -1164,19 +1183,23 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
     // scan: T threads per particle, particles of the group in row order
     const int per_pass = (int)blockDim.x / T;
     const int sl = (int)threadIdx.x % T;
+    const int side = 2 * nr + 1;  // stencil cells per axis
     for (int pidx = (int)threadIdx.x / T; pidx < npart && (int)threadIdx.x < per_pass * T; pidx += per_pass) {
       int row = 0;
       while (pidx >= s_pb[row + 1]) ++row;
       const int64_t i = s_plo[row] + (pidx - s_pb[row]);
-      const int lx = (nc > 0 && i >= s_px1[row]) ? 1 : 0;
       const int ly = row % GY, lz = row / GY;
+      // the particle's own cell (the binning of B1) and its position inside it
+      int ccx = 0, ccy = 0, ccz = 0;
+      if (nc > 0) cell_of_pos<MIX>(p, R, i, cur, ccx, ccy, ccz);
+      const int lx = ccx - cx;
       // own staged position (each particle is a candidate of its own cell)
-      const int own_u = nc > 0 ? ((lz + 1) * UY + (ly + 1)) * UX + (lx + 1) : 0;
+      const int own_u = nc > 0 ? ((lz + nr) * UY + (ly + nr)) * UX + (lx + nr) : 0;
       const int own_q = s_ub[own_u] + (int)(i - s_ulo[own_u]);
       int32_t* lb = p.nbr + list_col(i >> 5, p.maxrows, T, (int)(i & 31) * T + sl);
       int k = 0;
       int b1 = 0, b2 = 0, b3 = 0;  // quad shift register of the list writer
-      const int nruns = nc > 0 ? 9 : 1;
+      const int nruns = nc > 0 ? side * side : 1;
       if constexpr (MIX) {
         const uint4 pq_i = p.pq[cur][i];
         const float sc = R.fxs;
@@ -1190,10 +1213,9 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         const uint32_t rl2_s = (uint32_t)__cvta_generic_to_shared(sh.rl2f);
         const int maxrows = p.maxrows;
         // position inside the own cell (the binning of B1: cell = (u * nc) >> 32,
-        // so the low word of u * nc is the fraction), for culling the
-        // neighbour cells that lie wholly beyond the largest list radius of
-        // this particle's row. A cell is at least r_list wide, so only the
-        // images at offsets -1, 0, +1 can come within reach.
+        // so the low word of u * nc is the fraction), for culling the rows and
+        // row ends that lie wholly beyond the largest list radius of this
+        // particle's row
         const float wc = R.cellw;
         const float f2w = wc * 2.3283064365386963e-10f;  // cell width / 2^32
         const float fxl = (float)(uint32_t)((uint64_t)pq_i.x * (uint64_t)nc) * f2w;
@@ -1203,14 +1225,16 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         for (int run = 0; run < nruns; ++run) {
           int qs = 0, qe = ncand;
           if (nc > 0) {
-            const int oy = run % 3 - 1, oz = run / 3 - 1;
-            const float ey = oy < 0 ? fyl : (oy > 0 ? wc - fyl : 0.0f);
-            const float ez = oz < 0 ? fzl : (oz > 0 ? wc - fzl : 0.0f);
+            const int oy = run % side - nr, oz = run / side - nr;
+            const float ey = face_dist(oy, fyl, wc), ez = face_dist(oz, fzl, wc);
             const float d2 = fmaf(ey, ey, ez * ez);
             if (d2 >= lcut) continue;  // the whole row is out of reach
-            const int us0 = ((lz + run / 3) * UY + (ly + run % 3)) * UX + lx;
-            qs = s_ub[us0 + (fmaf(fxl, fxl, d2) < lcut ? 0 : 1)];
-            qe = s_ub[us0 + (fmaf(wc - fxl, wc - fxl, d2) < lcut ? 3 : 2)];
+            int xl = -nr, xh = nr;
+            while (xl < 0 && fmaf(face_dist(xl, fxl, wc), face_dist(xl, fxl, wc), d2) >= lcut) ++xl;
+            while (xh > 0 && fmaf(face_dist(xh, fxl, wc), face_dist(xh, fxl, wc), d2) >= lcut) --xh;
+            const int us0 = ((lz + nr + oz) * UY + (ly + nr + oy)) * UX + lx + nr;
+            qs = s_ub[us0 + xl];
+            qe = s_ub[us0 + xh + 1];
           }
           if (rel)
             k = scan_run_mix<true>(st_s, rl2_s, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz, maxrows,
@@ -1224,12 +1248,26 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         const double4_32a pi = p.p4[cur][i];
         const int tb = (int)pi.w * p.ntypes;
         const double L = R.L, hL = 0.5 * R.L;
+        double lmax = 0.0;
+        for (int t = 0; t < p.ntypes; ++t) lmax = fmax(lmax, sh.rl2d[tb + t]);
+        // position inside the own cell, for the same culling as the mixed path
+        const double wc = R.L / (double)(nc > 0 ? nc : 1);
+        const double fxl = pi.x - ccx * wc, fyl = pi.y - ccy * wc, fzl = pi.z - ccz * wc;
+        const double lcut = (sqrt(lmax) + 1e-9 * wc) * (sqrt(lmax) + 1e-9 * wc);
+        auto fd = [&](int o, double f) { return o < 0 ? f + (-o - 1) * wc : (o > 0 ? (wc - f) + (o - 1) * wc : 0.0); };
         for (int run = 0; run < nruns; ++run) {
           int qs = 0, qe = ncand;
           if (nc > 0) {
-            const int us0 = ((lz + run / 3) * UY + (ly + run % 3)) * UX + lx;
-            qs = s_ub[us0];
-            qe = s_ub[us0 + 3];
+            const int oy = run % side - nr, oz = run / side - nr;
+            const double ey = fd(oy, fyl), ez = fd(oz, fzl);
+            const double d2 = ey * ey + ez * ez;
+            if (d2 >= lcut) continue;
+            int xl = -nr, xh = nr;
+            while (xl < 0 && fd(xl, fxl) * fd(xl, fxl) + d2 >= lcut) ++xl;
+            while (xh > 0 && fd(xh, fxl) * fd(xh, fxl) + d2 >= lcut) --xh;
+            const int us0 = ((lz + nr + oz) * UY + (ly + nr + oy)) * UX + lx + nr;
+            qs = s_ub[us0 + xl];
+            qe = s_ub[us0 + xh + 1];
           }
           for (int q = qs + sl; q < qe; q += T) {
             const double4_32a pj = st_d[q];

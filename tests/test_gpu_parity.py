@@ -88,13 +88,14 @@ def test_forces_32k_tiled_melt(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("group", ["1", "2", "4", "8"])
+@pytest.mark.parametrize("reach,group", [("1", "1"), ("1", "2"), ("1", "4"), ("1", "8"), ("2", "1"), ("2", "8"),
+                                         ("2", "16"), ("2", "64")])
 @pytest.mark.parametrize("n,tile", [(1000, 1), (4000, 1), (4000, 2)], ids=["1000", "4000", "32000-tiled"])
-def test_list_build_every_group_shape(prec, group, n, tile, monkeypatch):
-    """The list build works on groups of 1, 2, 4 or 8 cells (1x1x1, 2x1x1, 2x2x1, 2x2x2). Every shape,
-    on boxes of 3 cells per edge (exact fixed-point test), 5 (FP32 relative coordinates for single
-    cells, exact for groups) and 10 (relative coordinates for every shape), gives the oracle's forces
-    with every lane split."""
+def test_list_build_every_group_shape(prec, reach, group, n, tile, monkeypatch):
+    """The list build works on groups of 1 to 64 cells (1x1x1 ... 4x4x4) of full-width cells
+    (3x3x3 stencil, KAMD_CELL_REACH=1) or half-width cells (5x5x5 stencil, corners culled). Every
+    shape, on boxes of 3/5 cells per edge (exact fixed-point test) up to 10/21 (FP32 relative
+    coordinates), gives the oracle's forces with every lane split."""
     pos, vel, types, L = melted(n, 23 if n == 4000 else 22, nsteps=200)
     if tile > 1:
         shifts = np.array([[i, j, k] for i in range(tile) for j in range(tile) for k in range(tile)], dtype=float) * L
@@ -104,6 +105,7 @@ def test_list_build_every_group_shape(prec, group, n, tile, monkeypatch):
         L = tile * L
     f_ref, v_ref, _ = oracle.forces(pos, types, ka_params(), L)
     monkeypatch.setenv("KAMD_LIST_GROUP", group)
+    monkeypatch.setenv("KAMD_CELL_REACH", reach)
     for tpa in (1, 4):
         with make_system(len(pos), L, types, prec, tpa=tpa) as s:
             s.set_state(pos, vel)
