@@ -520,6 +520,14 @@ def main():
     achieved = flop_step * CHUNK / launch_s / 1e12
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * FP32_LANES_PER_SM * nsm * SM_MAX_MHZ * 1e6 / 1e12
+    # the force phase alone (md_time_forces), on the final state: the FP32 roofline of the force kernel
+    t_force = s.time_forces(100 if n_sys < 200000 else 20)
+    force_phase = {"seconds_per_eval": t_force, "achieved": flop_step / t_force / 1e12, "peak": peak,
+                   "unit": "TFLOP/s", "frac": flop_step / t_force / 1e12 / peak,
+                   "entries": entries, "pairs_within_cutoff": pairs,
+                   "note": "md_time_forces: pair sums over the force list and force stores of a step, no energies "
+                           "and no velocity/position update, each evaluation closed by a grid barrier; "
+                           "FLOPs = 26 per entry within r_c + 8 per other entry"}
     analysis = analysis_cost(torch, s) if args.workload == "ka1m" else None
     device_bytes = info["device_bytes"]
     e2e = None
@@ -589,6 +597,7 @@ def main():
                                                 if clk.get("sm_mhz") else None),
                      "kernel": f"md_persistent<{'fp64' if prec == 'fp64' else 'mixed'}> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
+        "force_phase": force_phase,
         "analysis_ms": analysis,
         "device_bytes": device_bytes,
         "cpu_baseline": cpu,

@@ -281,6 +281,20 @@ md_status md_autotune(md_system* sys, double dt, int64_t probe_steps, md_tuning*
 md_status md_autotune_skin(md_system* sys, double dt, int64_t probe_steps, double skin, md_tuning* best,
                            double* seconds_per_step);
 
+/*
+ * md_time_forces: measurement of the force phase alone. One persistent launch
+ * evaluates the forces of the current positions `repeats` times (the pair
+ * sums over the force list and the force stores of a time step, without the
+ * velocity update, the position update or energies), each evaluation closed
+ * by a grid barrier; a launch with one evaluation is timed too, and
+ * *seconds_per_eval = (t(repeats) - t(1)) / (repeats - 1), CUDA events on the
+ * system's stream. Lists are brought up to date first (not timed). The state
+ * is unchanged except for the stored forces, which are those of the current
+ * positions either way. 1 <= repeats <= 100000. (The paper has no
+ * counterpart: this is a measurement interface.)
+ */
+md_status md_time_forces(md_system* sys, int64_t repeats, double* seconds_per_eval);
+
 /* md_get_info: counters and sizes (synchronises the stream). */
 md_status md_get_info(md_system* sys, md_info* info);
 

@@ -30,7 +30,6 @@ struct md_system {
   int grid = 0;
   int maxrows = 0;
   int stage_cap = 0;  // candidates the list build stages per group (dynamic shared memory)
-  int gx = 1, gy = 1, gz = 1;  // cells per list-build group
   int64_t ncells = 0;
   bool have_state = false;
   // host mirrors
@@ -534,7 +533,7 @@ double rc_max(const md_system* s) {
 // whenever the tuning changes. Cells are at least half the outer list radius
 // wide, so the list build scans the 5 x 5 x 5 cells around a particle's own
 // (less volume than 27 cells of the full radius, and the corners are culled);
-// a box with fewer than 5 such cells per edge uses cells of the full radius
+// a box with fewer than 8 such cells per edge uses cells of the full radius
 // (3 x 3 x 3), and one with fewer than 3 of those an all-pairs scan.
 // KAMD_CELL_REACH=1 keeps cells of the full radius (for tests of that path).
 void layout_cells(md_system* s) {
@@ -546,9 +545,16 @@ void layout_cells(md_system* s) {
     RepDev& R = s->reps[r];
     int nr = reach;
     int nc = (int)std::min(std::floor(R.L / (rl / nr)), 1024.0);
-    if (nr == 2 && nc < 5) {
+    const int nc1 = (int)std::floor(R.L / rl);
+    // full-width cells where they fit 3 per edge and half-width cells fewer
+    // than 8 (measured on 8 replicas of N = 1000, L = 9.41: 6 half-width
+    // cells per edge were 13 % slower than 3 full-width ones), and where the
+    // box is too small for 5 half-width cells; half-width cells otherwise
+    // (N = 1000 with an outer radius of 3.7: 5 half-width cells per edge were
+    // twice as fast as an all-pairs scan)
+    if (nr == 2 && ((nc < 8 && nc1 >= 3) || nc < 5)) {
       nr = 1;
-      nc = (int)std::floor(R.L / rl);
+      nc = nc1;
     }
     if (nc < 3) nc = 0;
     R.nc = nc;
@@ -579,41 +585,42 @@ int list_capacity(const md_system* s) {
   return cap;
 }
 
-// List-build groups: as many neighbouring cells per CTA (1, 2, 4 or 8 as
-// 1x1x1, 2x1x1, 2x2x1, 2x2x2) as keep the CTA's threads busy at T threads
-// per particle. KAMD_LIST_GROUP (1, 2, 4 or 8) overrides the choice.
+// List-build groups, per replica: as many neighbouring cells per CTA (powers
+// of two up to 4 x 4 x 4, 4 x 4 in a plane) as T threads per particle fill to
+// at most 90 % of the CTA, from the replica's own cells (a batch can mix
+// half-width, full-width and no cells). KAMD_LIST_GROUP forces one size.
 void choose_groups(md_system* s) {
-  double occ = 0.0;  // particles per occupied cell (two dimensions: only the cells of the plane hold particles)
-  for (int r = 0; r < s->nrep; ++r) {
-    const RepDev& R = s->reps[r];
-    if (R.nc == 0) continue;
-    const double w = (double)R.cellw;
-    occ = std::max(occ, s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
-                                     : (double)s->n_per[r] / (R.L * R.L) * w * w);
-  }
-  // cells per group: a power of two up to 4 x 4 x 4 (4 x 4 in a plane)
   const int gmax = s->ndim == 3 ? 64 : 16;
-  int g = 1;
-  if (occ > 0.0) {
-    // 10 % headroom: a group whose particles overflow the CTA needs a second,
-    // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2)
-    const double fit = 0.9 * (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
-    while (2 * g <= gmax && 2 * g <= fit) g *= 2;
-  }
+  int forced = 0;
   if (const char* e = std::getenv("KAMD_LIST_GROUP")) {
     const int v = std::atoi(e);
-    if (v >= 1 && v <= gmax && (v & (v - 1)) == 0) g = v;
+    if (v >= 1 && v <= gmax && (v & (v - 1)) == 0) forced = v;
   }
-  // x doubles first, then y, then z (a plane: x and y only)
-  int gx = 1, gy = 1, gz = 1;
-  for (int k = 1; k < g; k *= 2) {
-    if (gx <= gy && (s->ndim == 2 || gx <= gz) && gx < 4) gx *= 2;
-    else if (gy <= gz || s->ndim == 2) gy *= 2;
-    else gz *= 2;
+  for (int r = 0; r < s->nrep; ++r) {
+    RepDev& R = s->reps[r];
+    int g = 1;
+    if (R.nc > 0) {
+      // particles per occupied cell (two dimensions: only the cells of the plane hold particles)
+      const double w = (double)R.cellw;
+      const double occ = s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
+                                      : (double)s->n_per[r] / (R.L * R.L) * w * w;
+      // 10 % headroom: a group whose particles overflow the CTA needs a second,
+      // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2)
+      const double fit = 0.9 * (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
+      while (2 * g <= gmax && 2 * g <= fit) g *= 2;
+    }
+    if (forced) g = forced;
+    // x doubles first, then y, then z (a plane: x and y only)
+    int gx = 1, gy = 1, gz = 1;
+    for (int k = 1; k < g; k *= 2) {
+      if (gx <= gy && (s->ndim == 2 || gx <= gz) && gx < 4) gx *= 2;
+      else if (gy <= gz || s->ndim == 2) gy *= 2;
+      else gz *= 2;
+    }
+    R.gx = gx;
+    R.gy = gy;
+    R.gz = gz;
   }
-  s->gx = gx;
-  s->gy = gy;
-  s->gz = gz;
 }
 
 // Staging area of the list build: the candidates of the cells around one
@@ -626,7 +633,7 @@ int stage_capacity(md_system* s) {
     const RepDev& R = s->reps[r];
     // occupied union cells (two dimensions: one plane of cells)
     const int e = 2 * R.nr;
-    const double nu = s->ndim == 3 ? (double)(s->gx + e) * (s->gy + e) * (s->gz + e) : (double)(s->gx + e) * (s->gy + e);
+    const double nu = s->ndim == 3 ? (double)(R.gx + e) * (R.gy + e) * (R.gz + e) : (double)(R.gx + e) * (R.gy + e);
     const double w = (double)R.cellw;
     const double occ = s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
                                     : (double)s->n_per[r] / (R.L * R.L) * w * w;
@@ -674,7 +681,8 @@ md_status alloc_cells_and_list(md_system* s, int cap_entries) {
     for (int r = 0; r < s->nrep; ++r) {
       const int nc = s->reps[r].nc;
       if (nc == 0) continue;
-      const int ng = ((nc + s->gx - 1) / s->gx) * ((nc + s->gy - 1) / s->gy) * ((nc + s->gz - 1) / s->gz);
+      const RepDev& R = s->reps[r];
+      const int ng = ((nc + R.gx - 1) / R.gx) * ((nc + R.gy - 1) / R.gy) * ((nc + R.gz - 1) / R.gz);
       for (int k = 0; k < ng; ++k) grp.push_back(make_int2(r, k));
     }
     s->ngroups = (int64_t)grp.size();
@@ -834,9 +842,6 @@ KParams make_params(const md_system* s) {
   p.cell_rep = s->d_cell_rep;
   p.ncells = s->ncells;
   p.stage_cap = s->stage_cap;
-  p.gx = s->gx;
-  p.gy = s->gy;
-  p.gz = s->gz;
   p.ccount = s->d_ccount;
   p.cstart = s->d_cstart;
   p.ccursor = s->d_ccursor;
@@ -1455,8 +1460,8 @@ md_status md_set_tuning(md_system* s, const md_tuning* t) {
   s->tun = *t;
   layout_cells(s);
   for (auto& R : s->reps) R.want_rebuild = 1;
+  s->stage_cap = stage_capacity(s);  // also picks each replica's group shape
   CKS(upload_reps(s));
-  s->stage_cap = stage_capacity(s);
   CKS(alloc_cells_and_list(s, list_capacity(s)));
   CKS(configure_grid(s));
   CKS(download_ctl(s));
@@ -1581,6 +1586,37 @@ md_status md_autotune_skin(md_system* s, double dt, int64_t probe_steps, double 
                            double* seconds_per_step) {
   if (!(skin >= 0.05) || !(skin < 2.0)) return fail(s, MD_ERR_INVALID_ARG, "skin must be in [0.05, 2)");
   return autotune_impl(s, dt, probe_steps, skin, best, seconds_per_step);
+}
+
+md_status md_time_forces(md_system* s, int64_t repeats, double* seconds_per_eval) {
+  if (!s || !seconds_per_eval) return fail(s, MD_ERR_INVALID_ARG, "NULL argument");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state: call md_set_state or md_init_lattice first");
+  if (repeats < 1 || repeats > 100000) return fail(s, MD_ERR_INVALID_ARG, "repeats must be in [1, 100000]");
+  // bring the lists up to date first (a rebuild would otherwise be timed too)
+  CKS(download_ctl(s));
+  if (s->ctl.drifted) return fail(s, MD_ERR_INVALID_ARG, "the state is between a position and a velocity update");
+  if (s->ctl.pending & (MD_FLAG_REBUILD | MD_FLAG_PRUNE))
+    CKS(run_op(s, MD_OP_REBUILD, MD_KIND_NVE, 0, 0, 0, 0, 0, 0, nullptr));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  md_status st = MD_OK;
+  float ms = 0.0f, ms1 = 0.0f;
+  // the launch's fixed cost (start, first barrier, end) is taken out by a
+  // launch with one evaluation: seconds = (t(repeats) - t(1)) / (repeats - 1)
+  for (int pass = 0; pass < 2 && st == MD_OK; ++pass) {
+    const int64_t k = pass == 0 ? 1 : repeats;
+    cudaEventRecord(e0, s->stream);
+    st = run_op(s, MD_OP_FORCE_REPEAT, MD_KIND_NVE, 0.0, k, 0, 0, 0, 0, nullptr);
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(pass == 0 ? &ms1 : &ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MD_OK) return st;
+  *seconds_per_eval = repeats > 1 ? (double)(ms - ms1) * 1e-3 / (double)(repeats - 1) : (double)ms * 1e-3;
+  return MD_OK;
 }
 
 md_status md_get_tuning(const md_system* s, md_tuning* t) {

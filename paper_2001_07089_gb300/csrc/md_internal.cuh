@@ -41,7 +41,7 @@
 #define MD_FLAG_TIMEOUT 8
 #define MD_FLAG_PRUNE 16
 
-enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3 };
+enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3, MD_OP_FORCE_REPEAT = 4 };
 enum { MD_KIND_NVE = 0, MD_KIND_NH = 1, MD_KIND_RESAMPLE = 2, MD_KIND_NH_EXACT = 3 };
 
 // Per-replica description and state (device resident, one per replica).
@@ -55,6 +55,7 @@ struct RepDev {
   int32_t tile0;    // first tile
   int32_t nc;       // cells per edge (0: list built by an all-pairs scan)
   int32_t nr;       // cells on each side that the list build scans: 2 (cells >= r_list / 2 wide) or 1
+  int32_t gx, gy, gz;  // cells per list-build group along x, y, z (1, 2 or 4 each; per replica)
   double L, invL;
   double fx64;      // 2^64 / L
   float Lf, fxs;    // L, L / 2^32
@@ -126,7 +127,6 @@ struct KParams {
   int ntiles;
   int T;               // lanes per particle
   int maxrows;         // list entries per column (capacity per particle = maxrows*T), a multiple of 4
-  int gx, gy, gz;      // cells per list-build group along x, y, z (1, 2 or 4 each)
   int dual;            // 1: inner list pruned from the outer one; 0: one list (skin_outer == skin)
   // interaction tables, index a*ntypes+b
   float tab_f[MD_MAXTYPES * MD_MAXTYPES][4];   // rc^2, sigma^2, 48 eps, 4 eps

@@ -1005,7 +1005,6 @@ __device__ __forceinline__ float face_dist(int o, float f, float w) {
 template <bool MIX>
 __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cur) {
   const int T = p.T, gsz = 32 * T;
-  const int GX = p.gx, GY = p.gy, GZ = p.gz;
   extern __shared__ __align__(32) unsigned char dyn[];
   const int stage_cap = p.stage_cap;
   double4_32a* st_d = reinterpret_cast<double4_32a*>(dyn);  // FP64: positions, then slots
@@ -1034,6 +1033,7 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
     if (g >= p.ngroups && R.nc != 0) continue;
     const int nc = R.nc;
     const int nr = R.nr;  // cells of the stencil on each side
+    const int GX = R.gx, GY = R.gy, GZ = R.gz;
     const int UX = GX + 2 * nr, UY = GY + 2 * nr, UZ = GZ + 2 * nr;
     int nu, nrows, cx = 0, cy = 0, cz = 0;
     if (nc > 0) {
@@ -1644,6 +1644,17 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
     if (p.op == MD_OP_REBUILD) { finish(false, fvalid); return; }
+    if (p.op == MD_OP_FORCE_REPEAT) {
+      // measurement: nsteps force evaluations of the current positions, as the
+      // step loop does them (pair sums and force stores, no energy, no
+      // partials), each closed by a grid barrier
+      for (int64_t k = 0; k < p.nsteps; ++k) {
+        force_phase<MIX>(p, sh, cur, KICK_NONE, false, p.part[0], true, false, false, step0);
+        if ((fl = grid_sync(p, sh, 18)) < 0) return;
+      }
+      finish(false, 1);
+      return;
+    }
     if (p.op == MD_OP_INITVEL) {
       // Maxwell-Boltzmann start: draw 0 at each replica's bath temperature,
       // then centre and rescale (steps 1-4 of Sec. "Statistical temperature bath")

@@ -34,7 +34,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
 EXPORTED = ("md_create", "md_create_batch", "md_create_batch_dim", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_msd_tw", "md_set_tuning", "md_get_tuning", "md_autotune",
             "md_autotune_skin",
-            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_forces_noalloc", "md_last_error",
+            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_time_forces", "md_forces_noalloc", "md_last_error",
             "md_destroy")
 
 
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
             "md_get_info": [P, ctypes.POINTER(md_info)],
             "md_count_pairs": [P, ctypes.POINTER(i64)],
             "md_selftest_barrier": [P, dbl],
+            "md_time_forces": [P, i64, ctypes.POINTER(dbl)],
             "md_forces_noalloc": [i64, P, P, c_int, dbl, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -259,6 +260,13 @@ def md_count_pairs(h):
     return c.value
 
 
+def md_time_forces(h, repeats):
+    """Seconds per force evaluation (the force phase alone, measured inside one launch)."""
+    sec = ctypes.c_double()
+    _check(load().md_time_forces(h, int(repeats), ctypes.byref(sec)), h)
+    return sec.value
+
+
 def md_selftest_barrier(h, timeout_s):
     """Returns the status code (MD_ERR_TIMEOUT expected) instead of raising."""
     return load().md_selftest_barrier(h, float(timeout_s))
@@ -412,3 +420,7 @@ class System:
 
     def count_pairs(self):
         return md_count_pairs(self._h)
+
+    def time_forces(self, repeats=100):
+        """Seconds per evaluation of the force phase alone (md_time_forces)."""
+        return md_time_forces(self._h, repeats)

@@ -94,8 +94,10 @@ def test_forces_32k_tiled_melt(prec):
 def test_list_build_every_group_shape(prec, reach, group, n, tile, monkeypatch):
     """The list build works on groups of 1 to 64 cells (1x1x1 ... 4x4x4) of full-width cells
     (3x3x3 stencil, KAMD_CELL_REACH=1) or half-width cells (5x5x5 stencil, corners culled). Every
-    shape, on boxes of 3/5 cells per edge (exact fixed-point test) up to 10/21 (FP32 relative
-    coordinates), gives the oracle's forces with every lane split."""
+    shape gives the oracle's forces with every lane split: N = 1000 is scanned whole (too small for
+    cells at the default outer skin), N = 4000 has 4 full-width or 9 half-width cells per edge, the
+    tiled N = 32 000 box 9 or 18 (staged fixed-point words where the group's neighbourhood spans
+    more than half the box, FP32 relative coordinates elsewhere)."""
     pos, vel, types, L = melted(n, 23 if n == 4000 else 22, nsteps=200)
     if tile > 1:
         shifts = np.array([[i, j, k] for i in range(tile) for j in range(tile) for k in range(tile)], dtype=float) * L
@@ -702,3 +704,31 @@ def test_device_footprint_counter_tracks_frees():
         after = s.info()["device_bytes"]
     assert 0 < base < 2 ** 31
     assert abs(again - base) <= 0.5 * base and abs(after - base) <= 0.5 * base
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_time_forces_leaves_the_trajectory_unchanged(prec):
+    """md_time_forces (the force phase alone, repeated inside one launch) reports a positive time,
+    leaves the stored forces at the oracle's, and the trajectory that follows is bitwise the one
+    without the measurement."""
+    pos, vel, types, L = melted(1000, 93, nsteps=100)
+    f_ref, _, _ = oracle.forces(pos, types, ka_params(), L)
+    runs = []
+    for measure in (False, True):
+        with make_system(1000, L, types, prec) as s:
+            s.set_state(pos, vel)
+            s.step_nve(0.005, 10)
+            if measure:
+                t = s.time_forces(20)
+                assert 0.0 < t < 1e-2
+            log = s.step_nve(0.005, 40, log_every=10)
+            runs.append((s.get_state(), log))
+    (a, la), (b, lb) = runs
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(la, lb)
+    with make_system(1000, L, types, prec) as s:
+        s.set_state(pos, vel)
+        s.time_forces(5)
+        f, _, _ = s.forces()
+    check_forces(f, f_ref, prec)
