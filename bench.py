@@ -344,8 +344,10 @@ def profiled_traffic(workload, tuning):
                 k, v = line[3:].split("`: ", 1)
                 fields[k] = v.strip().strip("`")
     try:
-        same = (fields.get("kernel_sources_sha256") == kernel_sources_digest()
-                and fields.get("tuning") == "{threads_per_atom},{block_size},{skin},{skin_outer}".format(**tuning))
+        t = fields.get("tuning", "").split(",")
+        want = [tuning["threads_per_atom"], tuning["block_size"], tuning["skin"], tuning["skin_outer"]]
+        same = (fields.get("kernel_sources_sha256") == kernel_sources_digest() and len(t) == 4
+                and all(abs(float(a) - float(b)) < 1e-9 for a, b in zip(t, want)))
         return float(fields["dram_bytes_per_launch"]) if same else None
     except (KeyError, ValueError):
         return None
