@@ -343,9 +343,13 @@ def test_batch_replicas_equal_standalone_runs(prec, red_tiles, monkeypatch):
 @pytest.mark.parametrize("skins", [None, (0.3, 0.3), (0.2, 0.5)], ids=["default", "one-list", "dual-0.2-0.5"])
 def test_rebuilds_keep_parity_over_long_nve(prec, skins):
     """400 NVE steps at T=2 cross many list rebuilds (and inner-list prunes, for two lists).
-    FP64 follows the oracle step by step; the mixed path does for the first 100 steps, after
-    which chaos amplifies FP32 rounding and the comparison is the size of the energy excursions
-    (the conservation statistics)."""
+    FP64 follows the oracle step by step over all 400 steps; the mixed path does for the first
+    100 steps, after which chaos amplifies FP32 rounding until the trajectories part. From there
+    on the mixed run is compared by its statistics in tests/test_gpu_longrun.py (drift, PE, T,
+    g(r) and MSD with run-to-run error bars); here it only has to stay a finite, bounded NVE run:
+    its energy may not wander further than the oracle's own largest excursion plus four times
+    the excursion of a random walk with the larger of the two runs' RMS step-to-step changes of
+    E_tot/N (sigma * sqrt(steps)): a bound that rounding noise of either size stays within."""
     pos, vel, types, L = melted(1000, 71, nsteps=100)
     ref = oracle.run(pos, vel, types, ka_params(), L, 0.005, 400, log_every=1)
     with make_system(1000, L, types, prec) as s:
@@ -365,9 +369,12 @@ def test_rebuilds_keep_parity_over_long_nve(prec, skins):
         assert thermo_rel(log[:100], ref["thermo"][:100], "etot_per_n", 4) <= TOL_E["mixed"]
         e_g = log["etot_per_n"][:, 0]
         e_r = ref["thermo"][:, 4]
+        assert np.all(np.isfinite(e_g))
         exc_g = np.max(np.abs(e_g - e_g[0]))
         exc_r = np.max(np.abs(e_r - e_r[0]))
-        assert exc_g <= 1.5 * exc_r + 1e-5, (exc_g, exc_r)
+        # step-to-step fluctuation of E_tot/N (integrator noise, the same physics on both sides)
+        noise = max(np.std(np.diff(e_g)), np.std(np.diff(e_r)))
+        assert exc_g <= exc_r + 4.0 * noise * np.sqrt(len(e_g)), (exc_g, exc_r, noise)
 
 
 def test_sampled_forces_one_million():
