@@ -504,6 +504,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    rebuilds0 = s.info()["rebuilds"]
     clocks = Clocks(dev)
     clocks.start()
     times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush, step=stepper(s, T))
@@ -530,6 +531,17 @@ def main():
                    "note": "md_time_forces: pair sums over the force list and force stores of a step, no energies "
                            "and no velocity/position update, each evaluation closed by a grid barrier; "
                            "FLOPs = 26 per entry within r_c + 8 per other entry"}
+    # the list build alone (md_time_lists), at the same state; its share of the timed steps follows
+    # from the rebuilds those steps made (warm-up steps included, which the timed steps dominate)
+    builds = info["rebuilds"] - rebuilds0
+    t_list = s.time_lists(10 if n_sys < 200000 else 4)
+    md_steps = CHUNK * (args.steps + args.warmup)
+    single = wk["kind"] == "single"  # replicas of a batch rebuild separately: no single count
+    list_build = {"seconds_per_build": t_list, "builds_per_md_step": builds / md_steps if single else None,
+                  "share_of_step": t_list * builds / md_steps / (launch_s / CHUNK) if single else None,
+                  "note": "md_time_lists: the Verlet-list build of a rebuild (after the cell sort) repeated "
+                          "inside one launch; share = seconds per build x builds per MD step / seconds per MD "
+                          "step of the timed launches"}
     analysis = analysis_cost(torch, s) if args.workload == "ka1m" else None
     device_bytes = info["device_bytes"]
     e2e = None
@@ -600,6 +612,7 @@ def main():
                      "kernel": f"md_persistent<{'fp64' if prec == 'fp64' else 'mixed'}> (one launch = 100 MD steps)",
                      "peak_note": "FP32 FMA: 2 flops x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"},
         "force_phase": force_phase,
+        "list_build": list_build,
         "analysis_ms": analysis,
         "device_bytes": device_bytes,
         "cpu_baseline": cpu,

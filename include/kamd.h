@@ -295,6 +295,22 @@ md_status md_autotune_skin(md_system* sys, double dt, int64_t probe_steps, doubl
  */
 md_status md_time_forces(md_system* sys, int64_t repeats, double* seconds_per_eval);
 
+/*
+ * md_time_lists: measurement of the Verlet-list build alone (the step that
+ * follows the cell sort of a rebuild). Every replica is marked for a rebuild;
+ * one persistent launch then sorts the cells and builds the lists, and builds
+ * the (outer) lists of the same cells `repeats` - 1 more times, each closed by
+ * a grid barrier. A launch with a single rebuild is timed too, and
+ * *seconds_per_build = (t(repeats) - t(1)) / (repeats - 1), CUDA events on
+ * the system's stream. Needs 2 <= repeats <= 10000. The state afterwards is
+ * that of a rebuild at the current positions: particles are re-sorted into
+ * their cells (the same reordering a rebuild in a run makes), positions,
+ * velocities and stored forces are unchanged as a set, and later force sums
+ * may differ from those of an uninterrupted run in the last bits (summation
+ * order). (The paper has no counterpart: this is a measurement interface.)
+ */
+md_status md_time_lists(md_system* sys, int64_t repeats, double* seconds_per_build);
+
 /* md_get_info: counters and sizes (synchronises the stream). */
 md_status md_get_info(md_system* sys, md_info* info);
 

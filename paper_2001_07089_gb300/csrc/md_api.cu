@@ -605,7 +605,10 @@ void choose_groups(md_system* s) {
       const double occ = s->ndim == 3 ? (double)s->n_per[r] / (R.L * R.L * R.L) * w * w * w
                                       : (double)s->n_per[r] / (R.L * R.L) * w * w;
       // 10 % headroom: a group whose particles overflow the CTA needs a second,
-      // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2)
+      // mostly idle pass (measured: 1.7x slower list build at N = 32 000, T = 2).
+      // Groups stop at 64 cells: the staging area of 128-cell groups (57 KB per
+      // CTA at N = 10^6) takes shared memory from the L1 cache that the force
+      // phase's gathers use (list build 20 % faster, force phase 8 % slower)
       const double fit = 0.9 * (double)s->tun.block_size / ((double)s->tun.threads_per_atom * occ);
       while (2 * g <= gmax && 2 * g <= fit) g *= 2;
     }
@@ -1616,6 +1619,36 @@ md_status md_time_forces(md_system* s, int64_t repeats, double* seconds_per_eval
   cudaEventDestroy(e1);
   if (st != MD_OK) return st;
   *seconds_per_eval = repeats > 1 ? (double)(ms - ms1) * 1e-3 / (double)(repeats - 1) : (double)ms * 1e-3;
+  return MD_OK;
+}
+
+md_status md_time_lists(md_system* s, int64_t repeats, double* seconds_per_build) {
+  if (!s || !seconds_per_build) return fail(s, MD_ERR_INVALID_ARG, "NULL argument");
+  if (!s->have_state) return fail(s, MD_ERR_INVALID_ARG, "no state: call md_set_state or md_init_lattice first");
+  if (repeats < 2 || repeats > 10000) return fail(s, MD_ERR_INVALID_ARG, "repeats must be in [2, 10000]");
+  CKS(download_ctl(s));
+  if (s->ctl.drifted) return fail(s, MD_ERR_INVALID_ARG, "the state is between a position and a velocity update");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  md_status st = MD_OK;
+  float ms = 0.0f, ms1 = 0.0f;
+  // both launches start with the same full rebuild, which the difference
+  // takes out with the launch's fixed cost
+  for (int pass = 0; pass < 2 && st == MD_OK; ++pass) {
+    const int64_t k = pass == 0 ? 1 : repeats;
+    st = mark_rebuild_all(s);
+    if (st != MD_OK) break;
+    cudaEventRecord(e0, s->stream);
+    st = run_op(s, MD_OP_LIST_REPEAT, MD_KIND_NVE, 0.0, k, 0, 0, 0, 0, nullptr);
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(pass == 0 ? &ms1 : &ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MD_OK) return st;
+  *seconds_per_build = (double)(ms - ms1) * 1e-3 / (double)(repeats - 1);
   return MD_OK;
 }
 

@@ -41,7 +41,8 @@
 #define MD_FLAG_TIMEOUT 8
 #define MD_FLAG_PRUNE 16
 
-enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3, MD_OP_FORCE_REPEAT = 4 };
+enum { MD_OP_FORCES = 0, MD_OP_STEPS = 1, MD_OP_REBUILD = 2, MD_OP_INITVEL = 3, MD_OP_FORCE_REPEAT = 4,
+       MD_OP_LIST_REPEAT = 5 };
 enum { MD_KIND_NVE = 0, MD_KIND_NH = 1, MD_KIND_RESAMPLE = 2, MD_KIND_NH_EXACT = 3 };
 
 // Per-replica description and state (device resident, one per replica).

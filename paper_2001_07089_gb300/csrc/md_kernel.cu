@@ -921,63 +921,63 @@ __device__ int block_exclusive_scan(Shared& sh, int v, int* total) {
   return before;
 }
 
-// Scan of one run of staged candidates [qs, qe) for column `sl` of one
-// particle, mixed path. The common test is against the largest list radius
-// of the particle's row (lmax); only the few candidates that pass it are
-// checked against their own pair radius (type in the top bits of w), the
-// particle itself is excluded (own_q) and the entry is stored.
-// REL: staged FP32 coordinates relative to the group's reference particle;
-// otherwise staged fixed-point words and exact integer differences.
-// Distance^2 of staged candidate q from the particle (mixed path); *w gets
-// the candidate's (type << 30) | slot word.
-template <bool REL>
-__device__ __forceinline__ float cand_r2(uint32_t st_s, int q, float x, float y, float z, const uint4& pq, float sc,
-                                         uint32_t* w) {
-  uint32_t c0, c1, c2, c3;
-  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3) : "r"(st_s + 16u * (uint32_t)q));
-  float dx, dy, dz;
-  if (REL) {
-    dx = x - __uint_as_float(c0);
-    dy = y - __uint_as_float(c1);
-    dz = z - __uint_as_float(c2);
+// Pair list radius^2 of one particle's row for a candidate whose staged word
+// carries its type in the top two bits (NT2: at most two types).
+template <bool NT2>
+__device__ __forceinline__ float lim_of(float l0, float l1, float l2, float l3, uint32_t w) {
+  if constexpr (NT2) {
+    return w >= (1u << 30) ? l1 : l0;
   } else {
-    dx = (float)(int)(pq.x - c0) * sc;
-    dy = (float)(int)(pq.y - c1) * sc;
-    dz = (float)(int)(pq.z - c2) * sc;
+    const uint32_t t = w >> 30;
+    const float a = (t & 1u) ? l1 : l0, b = (t & 1u) ? l3 : l2;
+    return (t & 2u) ? b : a;
   }
-  *w = c3;
-  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-template <bool REL>
-__device__ __forceinline__ int scan_run_mix(uint32_t st_s, uint32_t rl2_s, int qs, int qe, int T, float x, float y,
-                                            float z, uint4 pq, float sc, int tb, float lmax, int own_q, int32_t* col,
-                                            int gsz, int maxrows, int k, int& b1, int& b2, int& b3) {
-  // st_s, rl2_s: shared-window addresses of the staged candidates (16 bytes
-  // each) and of the list-radius table. Chunks of up to 32 of this column's
-  // candidates: a first, branch-free pass marks those within the largest list
-  // radius of the row (lmax) in a bit mask; a second pass visits only the
-  // marked ones, in candidate order, checks their pair radius and the
-  // self-exclusion and stores them. The costly accept path then runs once
-  // per near candidate instead of once per candidate for the whole warp.
-  for (int q0 = qs; q0 < qe; q0 += 32 * T) {
-    const int nq = min(32, (qe - q0 + T - 1) / T);
+// Scan of one run of staged candidates [qs, qe) for column `sl` of one
+// particle, mixed path: the candidates qs + sl, qs + sl + T, ... (T = 2^tsh)
+// in chunks of up to 32. A branch-free first pass tests each candidate
+// against its own pair radius (selected by its type bits) and marks the hits
+// in a bit mask; the particle itself is then cleared by index, and a second
+// pass stores the marked candidates in order, reading only their slot words.
+// REL: staged FP32 coordinates relative to the group's reference particle;
+// otherwise staged fixed-point words and exact integer differences.
+template <bool REL, bool NT2>
+__device__ __forceinline__ int scan_run_mix(uint32_t st_s, int qs, int qe, int tsh, float x, float y, float z,
+                                            const uint4& pq, float sc, float l0, float l1, float l2, float l3,
+                                            int own_q, int32_t* col, int gsz, int maxrows, int k, int& b1, int& b2,
+                                            int& b3) {
+  const int T = 1 << tsh;
+  for (int q0 = qs; q0 < qe; q0 += 32 << tsh) {
+    const int nq = min(32, (qe - q0 + T - 1) >> tsh);
     unsigned mask = 0u;
 #pragma unroll 4
     for (int u = 0; u < nq; ++u) {
-      uint32_t w;
-      const float r2 = cand_r2<REL>(st_s, q0 + u * T, x, y, z, pq, sc, &w);
-      mask |= (r2 < lmax ? 1u : 0u) << u;
+      uint32_t c0, c1, c2, c3;
+      asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3)
+                   : "r"(st_s + 16u * (uint32_t)(q0 + (u << tsh))));
+      float dx, dy, dz;
+      if constexpr (REL) {
+        dx = x - __uint_as_float(c0);
+        dy = y - __uint_as_float(c1);
+        dz = z - __uint_as_float(c2);
+      } else {
+        dx = (float)(int)(pq.x - c0) * sc;
+        dy = (float)(int)(pq.y - c1) * sc;
+        dz = (float)(int)(pq.z - c2) * sc;
+      }
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      mask |= (r2 < lim_of<NT2>(l0, l1, l2, l3, c3) ? 1u : 0u) << u;
     }
+    const int d = own_q - q0;
+    if (d >= 0 && (d & (T - 1)) == 0 && (d >> tsh) < nq) mask &= ~(1u << (d >> tsh));
     while (mask) {
       const int u = __ffs(mask) - 1;
       mask &= mask - 1u;
-      const int q = q0 + u * T;
       uint32_t w;
-      const float r2 = cand_r2<REL>(st_s, q, x, y, z, pq, sc, &w);
-      float lim;
-      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(lim) : "r"(rl2_s + 4u * (uint32_t)(tb + (int)(w >> 30))));
-      if (r2 < lim && q != own_q) list_push(col, gsz, maxrows, k, b1, b2, b3, (int)(w & 0x3fffffffu));
+      asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(st_s + 16u * (uint32_t)(q0 + (u << tsh)) + 12u));
+      list_push(col, gsz, maxrows, k, b1, b2, b3, (int)(w & 0x3fffffffu));
     }
   }
   return k;
@@ -987,6 +987,44 @@ __device__ __forceinline__ int scan_run_mix(uint32_t st_s, uint32_t rl2_s, int q
 // the nearest face of the cell o cells away along one axis (0 for its own).
 __device__ __forceinline__ float face_dist(int o, float f, float w) {
   return o < 0 ? f + (float)(-o - 1) * w : (o > 0 ? (w - f) + (float)(o - 1) * w : 0.0f);
+}
+
+// All runs of one particle, mixed path: each of the (2 nr + 1)^2 rows of its
+// neighbourhood that comes within the largest list radius (lcut, with a
+// rounding margin), trimmed at both ends to the cells that do; or, for a
+// replica without cells (nc == 0), the whole staged replica. u_own: staged
+// cell of the particle's own cell; (fx, fy, fz): its position inside that
+// cell. Returns the entries found; b1..b3 hold the writer's partial quad.
+template <bool REL, bool NT2>
+__device__ __forceinline__ int scan_particle_mix(uint32_t st_s, const int* s_ub, int ncand, int nc, int nr, int UX,
+                                                 int UY, int u_own, float fx, float fy, float fz, float wc,
+                                                 float lcut, int sl, int tsh, float x, float y, float z,
+                                                 const uint4& pq, float sc, float l0, float l1, float l2, float l3,
+                                                 int own_q, int32_t* col, int gsz, int maxrows, int& b1, int& b2,
+                                                 int& b3) {
+  if (nc == 0)
+    return scan_run_mix<REL, NT2>(st_s, sl, ncand, tsh, x, y, z, pq, sc, l0, l1, l2, l3, own_q, col, gsz, maxrows, 0,
+                                  b1, b2, b3);
+  // distances along x to the cells at the ends of a row (nr <= 2)
+  const float em2 = fx + wc, em1 = fx, ep1 = wc - fx, ep2 = (wc - fx) + wc;
+  int k = 0;
+  for (int oz = -nr; oz <= nr; ++oz) {
+    const float ez = face_dist(oz, fz, wc);
+    for (int oy = -nr; oy <= nr; ++oy) {
+      const float ey = face_dist(oy, fy, wc);
+      const float d2 = fmaf(ey, ey, ez * ez);
+      if (d2 >= lcut) continue;  // the whole row is out of reach
+      int xl = -nr, xh = nr;
+      if (xl == -2 && fmaf(em2, em2, d2) >= lcut) xl = -1;
+      if (xl == -1 && fmaf(em1, em1, d2) >= lcut) xl = 0;
+      if (xh == 2 && fmaf(ep2, ep2, d2) >= lcut) xh = 1;
+      if (xh == 1 && fmaf(ep1, ep1, d2) >= lcut) xh = 0;
+      const int us0 = u_own + (oz * UY + oy) * UX;  // the row's cell in the particle's own column
+      k = scan_run_mix<REL, NT2>(st_s, s_ub[us0 + xl] + sl, s_ub[us0 + xh + 1], tsh, x, y, z, pq, sc, l0, l1, l2,
+                                 l3, own_q, col, gsz, maxrows, k, b1, b2, b3);
+    }
+  }
+  return k;
 }
 
 // B6: Verlet lists, radius r_c,ab + skin, built per GROUP of up to GX x GY x
@@ -1206,12 +1244,12 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         const float x = (float)(int)(pq_i.x - ref.x) * sc;
         const float y = (float)(int)(pq_i.y - ref.y) * sc;
         const float z = (float)(int)(pq_i.z - ref.z) * sc;
-        const int tb = (int)pq_i.w * p.ntypes;
-        float lmax = 0.0f;
-        for (int t = 0; t < p.ntypes; ++t) lmax = fmaxf(lmax, sh.rl2f[tb + t]);
+        // this particle's row of pair list radii^2, by partner type
+        const float* rl = sh.rl2f + (int)pq_i.w * p.ntypes;
+        const int nty = p.ntypes;
+        const float l0 = rl[0], l1 = nty > 1 ? rl[1] : 0.0f, l2 = nty > 2 ? rl[2] : 0.0f, l3 = nty > 3 ? rl[3] : 0.0f;
+        const float lmax = fmaxf(fmaxf(l0, l1), fmaxf(l2, l3));
         const uint32_t st_s = (uint32_t)__cvta_generic_to_shared(dyn);
-        const uint32_t rl2_s = (uint32_t)__cvta_generic_to_shared(sh.rl2f);
-        const int maxrows = p.maxrows;
         // position inside the own cell (the binning of B1: cell = (u * nc) >> 32,
         // so the low word of u * nc is the fraction), for culling the rows and
         // row ends that lie wholly beyond the largest list radius of this
@@ -1222,27 +1260,15 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         const float fyl = (float)(uint32_t)((uint64_t)pq_i.y * (uint64_t)nc) * f2w;
         const float fzl = (float)(uint32_t)((uint64_t)pq_i.z * (uint64_t)nc) * f2w;
         const float lcut = (sqrtf(lmax) + 1e-3f * wc) * (sqrtf(lmax) + 1e-3f * wc);  // rounding margin
-        for (int run = 0; run < nruns; ++run) {
-          int qs = 0, qe = ncand;
-          if (nc > 0) {
-            const int oy = run % side - nr, oz = run / side - nr;
-            const float ey = face_dist(oy, fyl, wc), ez = face_dist(oz, fzl, wc);
-            const float d2 = fmaf(ey, ey, ez * ez);
-            if (d2 >= lcut) continue;  // the whole row is out of reach
-            int xl = -nr, xh = nr;
-            while (xl < 0 && fmaf(face_dist(xl, fxl, wc), face_dist(xl, fxl, wc), d2) >= lcut) ++xl;
-            while (xh > 0 && fmaf(face_dist(xh, fxl, wc), face_dist(xh, fxl, wc), d2) >= lcut) --xh;
-            const int us0 = ((lz + nr + oz) * UY + (ly + nr + oy)) * UX + lx + nr;
-            qs = s_ub[us0 + xl];
-            qe = s_ub[us0 + xh + 1];
-          }
-          if (rel)
-            k = scan_run_mix<true>(st_s, rl2_s, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz, maxrows,
-                                   k, b1, b2, b3);
-          else
-            k = scan_run_mix<false>(st_s, rl2_s, qs + sl, qe, T, x, y, z, pq_i, sc, tb, lmax, own_q, lb, gsz,
-                                    maxrows, k, b1, b2, b3);
-        }
+        const int tsh = __ffs(T) - 1;
+#define KAMD_SCAN(R_, N_)                                                                                         \
+  scan_particle_mix<R_, N_>(st_s, s_ub, ncand, nc, nr, UX, UY, own_u, fxl, fyl, fzl, wc, lcut, sl, tsh, x, y, z, pq_i, \
+                            sc, l0, l1, l2, l3, own_q, lb, gsz, p.maxrows, b1, b2, b3)
+        if (rel)
+          k = nty <= 2 ? KAMD_SCAN(true, true) : KAMD_SCAN(true, false);
+        else
+          k = nty <= 2 ? KAMD_SCAN(false, true) : KAMD_SCAN(false, false);
+#undef KAMD_SCAN
         if (sl == 0) p.xbq[i] = pq_i;
       } else {
         const double4_32a pi = p.p4[cur][i];
@@ -1644,6 +1670,18 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       if ((fl = grid_sync(p, sh, 108)) < 0) return;
     }
     if (p.op == MD_OP_REBUILD) { finish(false, fvalid); return; }
+    if (p.op == MD_OP_LIST_REPEAT) {
+      // measurement: the launch began with a rebuild of every replica (the
+      // host marks them all); nsteps - 1 more list builds of the same cells
+      // follow, each closed by a grid barrier. Positions do not move, so each
+      // build writes the same lists again.
+      for (int64_t k = 1; k < p.nsteps; ++k) {
+        build_lists<MIX>(p, sh, cur);
+        if ((fl = grid_sync(p, sh, 19)) < 0) return;
+      }
+      finish(false, fvalid);
+      return;
+    }
     if (p.op == MD_OP_FORCE_REPEAT) {
       // measurement: nsteps force evaluations of the current positions, as the
       // step loop does them (pair sums and force stores, no energy, no

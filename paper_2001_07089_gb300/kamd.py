@@ -34,7 +34,7 @@ THERMO_DTYPE = np.dtype([("step", np.int64), ("T", np.float64), ("pe_per_n", np.
 EXPORTED = ("md_create", "md_create_batch", "md_create_batch_dim", "md_set_state", "md_get_state", "md_init_lattice", "md_forces",
             "md_step_nve", "md_step_nvt", "md_rdf", "md_msd", "md_msd_tw", "md_set_tuning", "md_get_tuning", "md_autotune",
             "md_autotune_skin",
-            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_time_forces", "md_forces_noalloc", "md_last_error",
+            "md_get_info", "md_count_pairs", "md_selftest_barrier", "md_time_forces", "md_time_lists", "md_forces_noalloc", "md_last_error",
             "md_destroy")
 
 
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
             "md_count_pairs": [P, ctypes.POINTER(i64)],
             "md_selftest_barrier": [P, dbl],
             "md_time_forces": [P, i64, ctypes.POINTER(dbl)],
+            "md_time_lists": [P, i64, ctypes.POINTER(dbl)],
             "md_forces_noalloc": [i64, P, P, c_int, dbl, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -267,6 +268,13 @@ def md_time_forces(h, repeats):
     return sec.value
 
 
+def md_time_lists(h, repeats):
+    """Seconds per Verlet-list build (the list build alone, measured inside one launch)."""
+    sec = ctypes.c_double()
+    _check(load().md_time_lists(h, int(repeats), ctypes.byref(sec)), h)
+    return sec.value
+
+
 def md_selftest_barrier(h, timeout_s):
     """Returns the status code (MD_ERR_TIMEOUT expected) instead of raising."""
     return load().md_selftest_barrier(h, float(timeout_s))
@@ -424,3 +432,7 @@ class System:
     def time_forces(self, repeats=100):
         """Seconds per evaluation of the force phase alone (md_time_forces)."""
         return md_time_forces(self._h, repeats)
+
+    def time_lists(self, repeats=20):
+        """Seconds per Verlet-list build alone (md_time_lists); leaves the state as a rebuild does."""
+        return md_time_lists(self._h, repeats)

@@ -739,3 +739,30 @@ def test_time_forces_leaves_the_trajectory_unchanged(prec):
         s.time_forces(5)
         f, _, _ = s.forces()
     check_forces(f, f_ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_time_lists_leaves_a_rebuilt_state(prec):
+    """md_time_lists (the list build alone, repeated inside one launch after a full rebuild)
+    reports a positive time and leaves the state of a rebuild at unchanged positions: the forces
+    there are the oracle's, and the 40 steps that follow keep the energy of the run without the
+    measurement (the re-sort may change the summation order, so not bitwise). N = 4000: half-width
+    cells and several list-build groups."""
+    pos, vel, types, L = melted(4000, 94, nsteps=100)
+    logs = []
+    for measure in (False, True):
+        with make_system(4000, L, types, prec) as s:
+            s.set_state(pos, vel)
+            s.step_nve(0.005, 10)
+            if measure:
+                t = s.time_lists(5)
+                assert 0.0 < t < 1e-2
+                p, _, _ = s.get_state()
+                f, _, _ = s.forces()
+                f_ref, _, _ = oracle.forces(p, types, ka_params(), L)
+                check_forces(f, f_ref, prec)
+            logs.append(s.step_nve(0.005, 40, log_every=10))
+    a, b = logs
+    scale = np.abs(a["pe_per_n"]) + 1.5 * a["T"]
+    tol = 1e-5 if prec == "mixed" else 1e-10
+    assert np.all(np.abs(a["etot_per_n"] - b["etot_per_n"]) <= tol * scale)
