@@ -933,7 +933,6 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
   for (int attempt = 0; attempt < 8; ++attempt) {
     // clear the barrier counter and any error flag of an earlier launch (the
     // host mirror is current: every launch ends with a download of it)
-    s->ctl.bar_count = 0;
     s->ctl.pending &= MD_FLAG_REBUILD;
     s->ctl.err_where = 0;
     CKS(upload_ctl(s));
@@ -1716,7 +1715,6 @@ md_status md_selftest_barrier(md_system* s, double timeout_s) {
   if (!(timeout_s > 0) || timeout_s > 60) return fail(s, MD_ERR_INVALID_ARG, "timeout_s must be in (0, 60]");
   CKS(download_ctl(s));
   const CtlDev saved = s->ctl;
-  s->ctl.bar_count = 0;
   s->ctl.pending = 0;
   CKS(upload_ctl(s));
   KParams p = make_params(s);
@@ -1726,7 +1724,6 @@ md_status md_selftest_barrier(md_system* s, double timeout_s) {
   const int pend = s->ctl.pending;
   // restore the control block so the system stays usable
   s->ctl = saved;
-  s->ctl.bar_count = 0;
   CKS(upload_ctl(s));
   CK(cudaStreamSynchronize(s->stream));
   if (pend & MD_FLAG_TIMEOUT) return fail(s, MD_ERR_TIMEOUT, "barrier wait ran out as intended (self-test)");

@@ -82,9 +82,8 @@ struct RepDev {
 
 // Grid barrier and launch-wide control block.
 struct CtlDev {
-  unsigned int bar_count;
   unsigned int bar_gen;
-  int pending;          // flags raised during a phase (atomicOr)
+  int pending;          // bits 0..15: flags raised during a phase (atomicOr); 16..31: barrier arrivals
   int snap[2];          // pending as seen by the last arriver, per barrier parity
   int cur;              // parity of the current gather buffer
   int drifted;          // 1: positions at t+dt while velocities/forces are at t

@@ -47,6 +47,7 @@ struct Shared {
   double red[16][MD_NPART];
   int scan[32];
   int snap;
+  unsigned gen;  // grid barrier generation this CTA waits for next (thread 0)
   // SM-local work layout of this launch (see sm_layout)
   unsigned sm_bits[8];
   int sm_ok, sm_idx, sm_used, sm_cnt, sm_rank;
@@ -99,18 +100,23 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned x) {
 }
 
 // Grid barrier with a time limit (acquire/release on the generation word).
-// Returns the pending-flag snapshot taken by the last CTA to arrive
+// The arrival count shares the control word `pending` with the flags (count
+// in bits 16..31, flags in bits 0..15): a flag raised before a CTA arrives
+// precedes that arrival in the word's modification order, so the atomic of
+// the last CTA to arrive returns every flag of the phase, with no further
+// read. Thread 0 of each CTA keeps the generation it waits for in shared
+// memory (read once at launch). Returns the flags as seen by the last arriver
 // (identical for every CTA), or -1 after a timeout.
 __device__ int grid_sync(const KParams& p, Shared& sh, int where) {
   __syncthreads();
   if (threadIdx.x == 0) {
     CtlDev* c = p.ctl;
-    const unsigned g = ld_acquire_u32(&c->bar_gen);
-    const unsigned arrived = atom_add_acqrel_u32(&c->bar_count, 1u);
+    const unsigned g = sh.gen;
+    const unsigned old = atom_add_acqrel_u32(reinterpret_cast<unsigned*>(&c->pending), 1u << 16);
     int res = -1;
-    if (arrived == gridDim.x - 1) {
-      c->bar_count = 0;
-      const int pend = atomicOr(&c->pending, 0);
+    if ((old >> 16) == gridDim.x - 1) {
+      const int pend = (int)(old & 0xffffu);
+      atomicAnd(&c->pending, 0xffff);  // clear the count before the release
       c->snap[(g + 1) & 1] = pend;
       st_release_u32(&c->bar_gen, g + 1);
       res = pend;
@@ -132,6 +138,7 @@ __device__ int grid_sync(const KParams& p, Shared& sh, int where) {
         }
       }
     }
+    sh.gen = g + 1;
     sh.snap = res;
 #ifdef KAMD_PHASE_TIMERS
     // profiling builds only: time between consecutive barriers, charged to
@@ -934,14 +941,42 @@ __device__ __forceinline__ float lim_of(float l0, float l1, float l2, float l3, 
   }
 }
 
-// Scan of one run of staged candidates [qs, qe) for column `sl` of one
-// particle, mixed path: the candidates qs + sl, qs + sl + T, ... (T = 2^tsh)
-// in chunks of up to 32. A branch-free first pass tests each candidate
-// against its own pair radius (selected by its type bits) and marks the hits
-// in a bit mask; the particle itself is then cleared by index, and a second
-// pass stores the marked candidates in order, reading only their slot words.
+// First pass over one chunk of staged candidates q0, q0 + T, ..., nq of them
+// (nq <= 32, T = 2^tsh), mixed path: each is tested against its own pair
+// radius (selected by its type bits) and the hits are marked in a bit mask.
 // REL: staged FP32 coordinates relative to the group's reference particle;
 // otherwise staged fixed-point words and exact integer differences.
+template <bool REL, bool NT2>
+__device__ __forceinline__ unsigned chunk_mask(uint32_t st_s, int q0, int nq, int tsh, float x, float y, float z,
+                                               const uint4& pq, float sc, float l0, float l1, float l2, float l3) {
+  unsigned mask = 0u;
+#pragma unroll 4
+  for (int u = 0; u < nq; ++u) {
+    uint32_t c0, c1, c2, c3;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3)
+                 : "r"(st_s + 16u * (uint32_t)(q0 + (u << tsh))));
+    float dx, dy, dz;
+    if constexpr (REL) {
+      dx = x - __uint_as_float(c0);
+      dy = y - __uint_as_float(c1);
+      dz = z - __uint_as_float(c2);
+    } else {
+      dx = (float)(int)(pq.x - c0) * sc;
+      dy = (float)(int)(pq.y - c1) * sc;
+      dz = (float)(int)(pq.z - c2) * sc;
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    mask |= (r2 < lim_of<NT2>(l0, l1, l2, l3, c3) ? 1u : 0u) << u;
+  }
+  return mask;
+}
+
+// Scan of one run of staged candidates [qs, qe) for column `sl` of one
+// particle, mixed path: the candidates qs + sl, qs + sl + T, ... (T = 2^tsh)
+// in chunks of up to 32. The first pass (chunk_mask) marks the hits; the
+// particle itself is then cleared by index, and a second pass stores the
+// marked candidates in order, reading only their slot words.
 template <bool REL, bool NT2>
 __device__ __forceinline__ int scan_run_mix(uint32_t st_s, int qs, int qe, int tsh, float x, float y, float z,
                                             const uint4& pq, float sc, float l0, float l1, float l2, float l3,
@@ -950,26 +985,7 @@ __device__ __forceinline__ int scan_run_mix(uint32_t st_s, int qs, int qe, int t
   const int T = 1 << tsh;
   for (int q0 = qs; q0 < qe; q0 += 32 << tsh) {
     const int nq = min(32, (qe - q0 + T - 1) >> tsh);
-    unsigned mask = 0u;
-#pragma unroll 4
-    for (int u = 0; u < nq; ++u) {
-      uint32_t c0, c1, c2, c3;
-      asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                   : "=r"(c0), "=r"(c1), "=r"(c2), "=r"(c3)
-                   : "r"(st_s + 16u * (uint32_t)(q0 + (u << tsh))));
-      float dx, dy, dz;
-      if constexpr (REL) {
-        dx = x - __uint_as_float(c0);
-        dy = y - __uint_as_float(c1);
-        dz = z - __uint_as_float(c2);
-      } else {
-        dx = (float)(int)(pq.x - c0) * sc;
-        dy = (float)(int)(pq.y - c1) * sc;
-        dz = (float)(int)(pq.z - c2) * sc;
-      }
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      mask |= (r2 < lim_of<NT2>(l0, l1, l2, l3, c3) ? 1u : 0u) << u;
-    }
+    unsigned mask = chunk_mask<REL, NT2>(st_s, q0, nq, tsh, x, y, z, pq, sc, l0, l1, l2, l3);
     const int d = own_q - q0;
     if (d >= 0 && (d & (T - 1)) == 0 && (d >> tsh) < nq) mask &= ~(1u << (d >> tsh));
     while (mask) {
@@ -1025,6 +1041,75 @@ __device__ __forceinline__ int scan_particle_mix(uint32_t st_s, const int* s_ub,
     }
   }
   return k;
+}
+
+// One particle on two lanes (lane h of the pair, pmask the pair's lanes), T =
+// 1, mixed path, a replica with cells: lane h takes the rows h, h + 2, ... of
+// the particle's neighbourhood (row order as in scan_particle_mix, the same
+// culling). In each round both lanes test one chunk of up to 32 candidates of
+// their current row, trade their hit counts, and store their hits one after
+// the other (lane 0's first) with 4-byte stores, so the column fills without
+// gaps, in an order fixed by the data. Returns the column's length (the same
+// on both lanes).
+template <bool REL, bool NT2>
+__device__ __forceinline__ int scan_particle_pair_mix(uint32_t st_s, const int* s_ub, int nr, int UX, int UY,
+                                                      int u_own, float fx, float fy, float fz, float wc, float lcut,
+                                                      int h, unsigned pmask, float x, float y, float z,
+                                                      const uint4& pq, float sc, float l0, float l1, float l2,
+                                                      float l3, int own_q, int32_t* col, int gsz, int maxrows) {
+  const float em2 = fx + wc, em1 = fx, ep1 = wc - fx, ep2 = (wc - fx) + wc;
+  int oy = -nr + h - 2, oz = -nr;  // row cursor: advanced by two rows before use
+  int q0 = 0, qe = 0;
+  // move to this lane's next row that has candidates within reach
+  auto next_row = [&]() -> bool {
+    while (true) {
+      oy += 2;
+      if (oy > nr) {
+        oy -= 2 * nr + 1;
+        ++oz;
+      }
+      if (oz > nr) return false;
+      const float ez = face_dist(oz, fz, wc), ey = face_dist(oy, fy, wc);
+      const float d2 = fmaf(ey, ey, ez * ez);
+      if (d2 >= lcut) continue;
+      int xl = -nr, xh = nr;
+      if (xl == -2 && fmaf(em2, em2, d2) >= lcut) xl = -1;
+      if (xl == -1 && fmaf(em1, em1, d2) >= lcut) xl = 0;
+      if (xh == 2 && fmaf(ep2, ep2, d2) >= lcut) xh = 1;
+      if (xh == 1 && fmaf(ep1, ep1, d2) >= lcut) xh = 0;
+      const int us0 = u_own + (oz * UY + oy) * UX;
+      q0 = s_ub[us0 + xl];
+      qe = s_ub[us0 + xh + 1];
+      if (q0 < qe) return true;
+    }
+  };
+  bool have = next_row();
+  int k = 0;
+  while (true) {
+    unsigned mask = 0u;
+    const int base = q0;
+    if (have) {
+      const int nq = min(32, qe - q0);
+      mask = chunk_mask<REL, NT2>(st_s, q0, nq, 0, x, y, z, pq, sc, l0, l1, l2, l3);
+      const int d = own_q - q0;
+      if (d >= 0 && d < nq) mask &= ~(1u << d);
+      q0 += nq;
+      if (q0 >= qe) have = next_row();
+    }
+    const int c = __popc(mask);
+    const int other = __shfl_xor_sync(pmask, (c << 1) | (have ? 1 : 0), 1);
+    int e = k + (h ? (other >> 1) : 0);
+    while (mask) {
+      const int u = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      uint32_t w;
+      asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(st_s + 16u * (uint32_t)(base + u) + 12u));
+      if (e < maxrows) col[list_at(0, e, gsz)] = (int)(w & 0x3fffffffu);
+      ++e;
+    }
+    k += c + (other >> 1);
+    if (!have && !(other & 1)) return k;
+  }
 }
 
 // B6: Verlet lists, radius r_c,ab + skin, built per GROUP of up to GX x GY x
@@ -1218,11 +1303,17 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
       }
     }
     __syncthreads();
-    // scan: T threads per particle, particles of the group in row order
-    const int per_pass = (int)blockDim.x / T;
-    const int sl = (int)threadIdx.x % T;
+    // scan: T threads per particle, particles of the group in row order; with
+    // T = 1 and at most half as many particles as threads (mixed path, cells),
+    // two lanes per particle (scan_particle_pair_mix)
+    const bool pair = MIX && T == 1 && nc > 0 && 2 * npart <= (int)blockDim.x;
+    const int lanes = pair ? 2 : T;
+    const int per_pass = (int)blockDim.x / lanes;
+    const int sl = pair ? 0 : (int)threadIdx.x % T;
+    const int h = pair ? (int)(threadIdx.x & 1u) : 0;
     const int side = 2 * nr + 1;  // stencil cells per axis
-    for (int pidx = (int)threadIdx.x / T; pidx < npart && (int)threadIdx.x < per_pass * T; pidx += per_pass) {
+    for (int pidx = (int)threadIdx.x / lanes; pidx < npart && (int)threadIdx.x < per_pass * lanes;
+         pidx += per_pass) {
       int row = 0;
       while (pidx >= s_pb[row + 1]) ++row;
       const int64_t i = s_plo[row] + (pidx - s_pb[row]);
@@ -1264,12 +1355,24 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
 #define KAMD_SCAN(R_, N_)                                                                                         \
   scan_particle_mix<R_, N_>(st_s, s_ub, ncand, nc, nr, UX, UY, own_u, fxl, fyl, fzl, wc, lcut, sl, tsh, x, y, z, pq_i, \
                             sc, l0, l1, l2, l3, own_q, lb, gsz, p.maxrows, b1, b2, b3)
-        if (rel)
-          k = nty <= 2 ? KAMD_SCAN(true, true) : KAMD_SCAN(true, false);
-        else
-          k = nty <= 2 ? KAMD_SCAN(false, true) : KAMD_SCAN(false, false);
+#define KAMD_SCAN2(R_, N_)                                                                                           \
+  scan_particle_pair_mix<R_, N_>(st_s, s_ub, nr, UX, UY, own_u, fxl, fyl, fzl, wc, lcut, h,                         \
+                                 3u << (threadIdx.x & 30u), x, y, z, pq_i, sc, l0, l1, l2, l3, own_q, lb, gsz,        \
+                                 p.maxrows)
+        if (pair) {
+          if (rel)
+            k = nty <= 2 ? KAMD_SCAN2(true, true) : KAMD_SCAN2(true, false);
+          else
+            k = nty <= 2 ? KAMD_SCAN2(false, true) : KAMD_SCAN2(false, false);
+        } else {
+          if (rel)
+            k = nty <= 2 ? KAMD_SCAN(true, true) : KAMD_SCAN(true, false);
+          else
+            k = nty <= 2 ? KAMD_SCAN(false, true) : KAMD_SCAN(false, false);
+        }
 #undef KAMD_SCAN
-        if (sl == 0) p.xbq[i] = pq_i;
+#undef KAMD_SCAN2
+        if (sl == 0 && h == 0) p.xbq[i] = pq_i;
       } else {
         const double4_32a pi = p.p4[cur][i];
         const int tb = (int)pi.w * p.ntypes;
@@ -1308,9 +1411,11 @@ __device__ __forceinline__ void build_lists(const KParams& p, Shared& sh, int cu
         }
         if (sl == 0) p.xbd[i] = pi;
       }
-      list_flush(lb, gsz, p.maxrows, k, b1, b2, b3);
-      if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
-      p.nnb[i * T + sl] = min(k, p.maxrows);
+      if (!pair) list_flush(lb, gsz, p.maxrows, k, b1, b2, b3);
+      if (h == 0) {
+        if (k > p.maxrows) raise_flag(p, MD_FLAG_OVERFLOW);
+        p.nnb[i * T + sl] = min(k, p.maxrows);
+      }
     }
     __syncthreads();
   }
@@ -1631,6 +1736,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
   if (threadIdx.x < 8) sh.sm_bits[threadIdx.x] = 0u;
   if (threadIdx.x == 0) p.cta_sm[blockIdx.x] = sm_id();
   CtlDev* C = p.ctl;
+  if (threadIdx.x == 0) sh.gen = ld_acquire_u32(&C->bar_gen);
   int cur = C->cur;
   const int drifted = C->drifted;
   const int fvalid = C->forces_valid;
@@ -1774,6 +1880,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
 __global__ void k_barrier_selftest(KParams p) {
   __shared__ Shared sh;
   if (blockIdx.x == 0) return;
+  if (threadIdx.x == 0) sh.gen = ld_acquire_u32(&p.ctl->bar_gen);
   (void)grid_sync(p, sh, 200);
 }
 
