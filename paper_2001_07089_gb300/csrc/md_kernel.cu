@@ -943,7 +943,8 @@ __device__ __forceinline__ float lim_of(float l0, float l1, float l2, float l3, 
 
 // First pass over one chunk of staged candidates q0, q0 + T, ..., nq of them
 // (nq <= 32, T = 2^tsh), mixed path: each is tested against its own pair
-// radius (selected by its type bits) and the hits are marked in a bit mask.
+// radius (selected by its type bits) and the hits are marked in a bit mask
+// (bit u: candidate q0 + u T).
 // REL: staged FP32 coordinates relative to the group's reference particle;
 // otherwise staged fixed-point words and exact integer differences.
 template <bool REL, bool NT2>
@@ -967,9 +968,12 @@ __device__ __forceinline__ unsigned chunk_mask(uint32_t st_s, int q0, int nq, in
       dz = (float)(int)(pq.z - c2) * sc;
     }
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    mask |= (r2 < lim_of<NT2>(l0, l1, l2, l3, c3) ? 1u : 0u) << u;
+    // hit: r2 - lim < 0 (the sign of a rounded difference is that of the
+    // exact one, and equal values give +0), shifted in from the top
+    const float d = r2 - lim_of<NT2>(l0, l1, l2, l3, c3);
+    mask = (mask >> 1) | (__float_as_uint(d) & 0x80000000u);
   }
-  return mask;
+  return nq > 0 ? mask >> (32 - nq) : 0u;  // candidate u at bit u
 }
 
 // Scan of one run of staged candidates [qs, qe) for column `sl` of one
