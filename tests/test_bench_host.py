@@ -67,7 +67,9 @@ def test_traffic_only_for_current_sources_and_tuning(tmp_path, monkeypatch):
 
 def test_committed_summaries_carry_the_fields_the_bench_reads():
     prof = os.path.join(bench.ROOT, "profiles")
-    names = [n for n in os.listdir(prof) if n.startswith("md_persistent_") and n.endswith(".md")]
+    # the per-workload launch summaries that profiled_traffic reads (other summaries, such as a
+    # phase timed alone, carry no traffic fields)
+    names = [n for n in os.listdir(prof) if n in {f"md_persistent_{w}.md" for w in bench.WORKLOADS}]
     assert names
     for n in names:
         text = open(os.path.join(prof, n)).read()
