@@ -739,16 +739,20 @@ __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t
 
 // Sum of the partial records [u0, u0 + nu) (fixed order): thread-strided
 // float-float (mixed) or double accumulation, warp trees, then the CTA's
-// warps in order. Thread 0 receives the six totals in acc.
+// warps in order; the warps' sums are added by lanes 0..5 of warp 0, one
+// quantity each (each sum in the same order as one thread adding them one
+// after the other). Thread 0 receives the six totals in acc.
 template <bool MIX>
 __device__ void sum_records(Shared& sh, const double* part, int64_t u0, int64_t nu, double* acc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t B = blockDim.x;
+  double tot = 0.0;  // lane k < 6 of warp 0: total of quantity k
   if constexpr (MIX) {
     ff a[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) a[k] = ff{0.f, 0.f};
     const float2* q0 = reinterpret_cast<const float2*>(part);
-    for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+    for (int64_t t = threadIdx.x; t < nu; t += B) {
       const float2* q = q0 + (u0 + t) * MD_NPART;
 #pragma unroll
       for (int k = 0; k < 6; ++k) a[k] = ff_add(a[k], ff{q[k].x, q[k].y});
@@ -760,35 +764,37 @@ __device__ void sum_records(Shared& sh, const double* part, int64_t u0, int64_t 
       if (lane == 0) red[warp * MD_NPART + k] = make_float2(a[k].hi, a[k].lo);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        ff t = {red[k].x, red[k].y};
-        for (int w = 1; w < nwarp; ++w) t = ff_add(t, ff{red[w * MD_NPART + k].x, red[w * MD_NPART + k].y});
-        acc[k] = (double)t.hi + (double)t.lo;
-      }
+    if (warp == 0 && lane < 6) {
+      ff u = {red[lane].x, red[lane].y};
+      for (int w = 1; w < nwarp; ++w) u = ff_add(u, ff{red[w * MD_NPART + lane].x, red[w * MD_NPART + lane].y});
+      tot = (double)u.hi + (double)u.lo;
     }
   } else {
+    double a[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-    for (int64_t t = threadIdx.x; t < nu; t += blockDim.x) {
+    for (int k = 0; k < 6; ++k) a[k] = 0.0;
+    for (int64_t t = threadIdx.x; t < nu; t += B) {
       const double* q = part + (u0 + t) * MD_NPART;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] += q[k];
+      for (int k = 0; k < 6; ++k) a[k] += q[k];
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      acc[k] = warp_sum(acc[k]);
-      if (lane == 0) sh.red[warp][k] = acc[k];
+      a[k] = warp_sum(a[k]);
+      if (lane == 0) sh.red[warp][k] = a[k];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0 && lane < 6) {
+      double u = sh.red[0][lane];
+      for (int w = 1; w < nwarp; ++w) u += sh.red[w][lane];
+      tot = u;
+    }
+  }
+  if (warp == 0) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        double t = sh.red[0][k];
-        for (int w = 1; w < nwarp; ++w) t += sh.red[w][k];
-        acc[k] = t;
-      }
+    for (int k = 0; k < 6; ++k) {
+      const double v = __shfl_sync(0xffffffffu, tot, k);
+      if (lane == 0) acc[k] = v;
     }
   }
   __syncthreads();
