@@ -103,6 +103,12 @@ struct md_system {
   // the persistent launch as an instantiated CUDA graph (one cooperative
   // kernel node whose parameters are updated per call)
   bool use_graph = true;
+  // partial records of NVE log steps reduced after the launch (size in doubles)
+  double* d_plog = nullptr;
+  longlong2* d_plog_rec = nullptr;
+  size_t plog_cap = 0;
+  int plog_slots = 0;
+  bool log_now = false;  // KAMD_LOG_NOW=1: every log record reduced at its step
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaGraphNode_t gnode = nullptr;
@@ -865,6 +871,10 @@ KParams make_params(const md_system* s) {
   p.nnb_in = p.dual ? s->d_nnb_in : s->d_nnb;
   p.part[0] = s->d_part[0];
   p.part[1] = s->d_part[1];
+  p.plog = s->d_plog;
+  p.plog_rec = s->d_plog_rec;
+  p.plog_stride = (int64_t)s->ntiles * s->tun.threads_per_atom * MD_NPART;
+  p.plog_slots = (s->plog_slots > 0 && (size_t)s->plog_slots * (size_t)p.plog_stride <= s->plog_cap) ? s->plog_slots : 0;
   return p;
 }
 
@@ -952,6 +962,9 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
     CKS(download_ctl(s));
     if (op == MD_OP_STEPS) done += s->ctl.steps_done;
     const int pend = s->ctl.pending;
+    // log records whose sums the launch left in slots (before a relaunch reuses them)
+    if (!(pend & MD_FLAG_TIMEOUT) && s->ctl.log_slots_used > 0)
+      CK(md_launch_log_records(s->mixed, p, s->ctl.log_slots_used, s->tun.block_size, s->stream));
     if (pend & MD_FLAG_TIMEOUT) {
       s->have_state = false;
       char buf[160];
@@ -1129,6 +1142,7 @@ md_status md_create_batch_dim(int ndim, int nrep, const int64_t* n_per, const do
   }
   if (const char* e = std::getenv("KAMD_BARRIER_TIMEOUT_MS")) s->timeout_ns = (unsigned long long)std::atoll(e) * 1000000ull;
   if (const char* e = std::getenv("KAMD_NO_GRAPH")) s->use_graph = !(e[0] == '1');
+  if (const char* e = std::getenv("KAMD_LOG_NOW")) s->log_now = e[0] == '1';
   cudaError_t ce = cudaGetDevice(&s->device);
   if (ce != cudaSuccess) return destroy_fail(s, cuda_fail(s, ce, "cudaGetDevice"));
   int major = 0, minor = 0, coop = 0;
@@ -1180,6 +1194,7 @@ md_status md_create_batch_dim(int ndim, int nrep, const int64_t* n_per, const do
     if (st != MD_OK) return destroy_fail(s, st);       \
   } while (0)
   AL(s->d_reps, (size_t)nrep);
+  AL(s->d_plog_rec, (size_t)MD_LOG_SLOTS);
   AL(s->d_tile_rep, (size_t)s->ntiles);
   AL(s->d_ctl, 1);
   if (s->mixed) {
@@ -1335,8 +1350,26 @@ static md_status step_common(md_system* s, int kind, double dt, int64_t nsteps, 
   if (log && log_every <= 0) return fail(s, MD_ERR_INVALID_ARG, "log_every must be > 0 when log is given");
   const int64_t nlog = (log && log_every > 0) ? nsteps / log_every : 0;
   CKS(ensure_thermo(s, nlog * s->nrep));
+  // room for the partial records of up to MD_LOG_SLOTS NVE log steps per
+  // launch (at most 256 MB), reduced after the launch's last step; the
+  // Nose-Hoover kinds reduce every step anyway
+  int slots = 0;
+  if (nlog > 0 && kind != MD_KIND_NH && kind != MD_KIND_NH_EXACT && !s->log_now) {
+    const size_t stride = (size_t)s->ntiles * s->tun.threads_per_atom * MD_NPART;
+    const size_t most = ((size_t)256 << 20) / sizeof(double) / stride;
+    slots = (int)std::min<int64_t>(std::min<int64_t>(nlog, MD_LOG_SLOTS), (int64_t)most);
+    if (slots > 0 && (size_t)slots * stride > s->plog_cap) {
+      dfree(s, s->d_plog);
+      s->d_plog = nullptr;
+      s->plog_cap = 0;
+      CKS(dalloc(s, &s->d_plog, (size_t)slots * stride));
+      s->plog_cap = (size_t)slots * stride;
+    }
+  }
+  s->plog_slots = slots;
   int64_t done = 0;
   md_status st = run_op(s, MD_OP_STEPS, kind, dt, nsteps, nstep_boltz, seed, log ? log_every : 0, nlog, &done);
+  s->plog_slots = 0;
   if (st != MD_OK) return st;
   if (nlog > 0) {
     CK(cudaMemcpyAsync(log, s->d_thermo, sizeof(ThermoDev) * nlog * s->nrep, cudaMemcpyDeviceToHost, s->stream));
@@ -1762,7 +1795,7 @@ void md_destroy(md_system* s) {
   dfree(s, s->d_tpfx); dfree(s, s->d_tp4); dfree(s, s->d_tvel); dfree(s, s->d_tfrc); dfree(s, s->d_tgid); dfree(s, s->d_ttyp);
   dfree(s, s->d_timg);
   dfree(s, s->d_cellof); dfree(s, s->d_cell_rep); dfree(s, s->d_ccount); dfree(s, s->d_cstart); dfree(s, s->d_ccursor); dfree(s, s->d_chunk); dfree(s, s->d_cta_sm); dfree(s, s->d_grp); dfree(s, s->d_redmap); dfree(s, s->d_redrep); dfree(s, s->d_redpart); dfree(s, s->d_scat);
-  dfree(s, s->d_nbr); dfree(s, s->d_nnb); dfree(s, s->d_part[0]); dfree(s, s->d_part[1]);
+  dfree(s, s->d_nbr); dfree(s, s->d_nnb); dfree(s, s->d_part[0]); dfree(s, s->d_part[1]); dfree(s, s->d_plog); dfree(s, s->d_plog_rec);
   dfree(s, s->d_typ_caller); dfree(s, s->d_rep_of_caller); dfree(s, s->d_thermo); dfree(s, s->d_io);
   dfree(s, s->d_io_i); dfree(s, s->d_rdf); dfree(s, s->d_msd_part); dfree(s, s->d_count);
   for (int k = 0; k < MD_MSD_SLOTS; ++k) dfree(s, s->d_msd_ref[k]);

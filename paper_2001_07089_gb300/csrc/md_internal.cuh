@@ -30,6 +30,7 @@
 #define MD_MAXTYPES 4
 #define MD_SCAN_CHUNK 1024  // cells per chunk of the cell-count scan
 #define MD_UNION_MAX 512    // staged cells of one list-build group: (GX+2nr)(GY+2nr)(GZ+2nr) <= 8*8*8
+#define MD_LOG_SLOTS 64     // log steps per launch whose reductions wait for the launch end
 #define MD_ROWS_MAX 16      // (y, z) rows of cells in one list-build group: GY*GZ <= 4*4
 #define MD_RED_TILES 256    // tiles per chunk of the two-level per-replica reduction (default)
 #define MD_NPART 8   // per-tile partial sums: pe, ke, vir, px, py, pz, (2 spare)
@@ -87,6 +88,7 @@ struct CtlDev {
   int snap[2];          // pending as seen by the last arriver, per barrier parity
   int cur;              // parity of the current gather buffer
   int drifted;          // 1: positions at t+dt while velocities/forces are at t
+  int log_slots_used;   // log slots the last launch filled (their records still to form)
   int forces_valid;
   int64_t step;         // global step counter
   int64_t steps_done;   // steps completed by the current/last launch
@@ -204,10 +206,17 @@ struct KParams {
   int32_t* nnb_in;
   // reductions
   double* part[2];     // [ntiles][MD_NPART]: doubles (FP64 path) or float (hi, lo) pairs (mixed path)
+  // partial records of NVE steps that only log, reduced after the launch's
+  // last step: plog_slots slots of plog_stride doubles each
+  double* plog;
+  longlong2* plog_rec;  // per slot: (step, log record index)
+  int64_t plog_stride;
+  int plog_slots;
 };
 
 // Host-side launchers (md_kernel.cu).
 cudaError_t md_launch_persistent(bool mixed, const KParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t md_launch_log_records(bool mixed, const KParams& p, int nslots, int block, cudaStream_t s);
 cudaError_t md_occupancy(bool mixed, int block, size_t smem, int* blocks_per_sm);
 const void* md_persistent_fn(bool mixed);
 cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s);

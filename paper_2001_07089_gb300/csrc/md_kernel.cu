@@ -33,7 +33,7 @@
 namespace kamd {
 
 enum { KICK_NONE = 0, KICK_VV = 1, KICK_NH = 2, KICK_NH_EXACT = 3 };
-enum { RED_FORCES = 0, RED_KE = 1, RED_STEP = 2, RED_RESAMPLE = 3, RED_STEP_KE = 4 };
+enum { RED_FORCES = 0, RED_KE = 1, RED_STEP = 2, RED_RESAMPLE = 3, RED_STEP_KE = 4, RED_LOG = 5 };
 
 struct Shared {
   float4 tabf[MD_MAXTYPES * MD_MAXTYPES];
@@ -846,6 +846,22 @@ __device__ bool reduce_phase(const KParams& p, Shared& sh, const double* part, i
 __device__ __noinline__ void reduce_scalars(const KParams& p, RepDev& R, int64_t r, const double* acc, int mode,
                                             int64_t step, bool log_now, int64_t log_idx, bool nh) {
   const double n = (double)R.n, X = (double)p.ndim * n, dt = p.dt;
+  if (mode == RED_LOG) {
+    // the log record of an NVE step reduced after the launch's last step: the
+    // same values as the record written at the step, the replica untouched
+    const double pe = acc[0], ke = acc[1];
+    ThermoDev th;
+    th.step = step;
+    th.T = 2.0 * ke / X;
+    th.pe_per_n = pe / n;
+    th.ke_per_n = ke / n;
+    th.etot_per_n = (ke + pe) / n;
+    th.virial = acc[2];
+    th.h_nh = ke + pe + 0.0;
+    th.xi = 0.0;
+    if (p.thermo) p.thermo[log_idx * p.nrep + r] = th;
+    return;
+  }
   if (mode == RED_RESAMPLE) {
     const double mx = acc[0] / n, my = acc[1] / n, mz = acc[2] / n;
     const double S = acc[3] - n * (mx * mx + my * my + mz * mz);
@@ -1758,6 +1774,12 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
   const int kick = p.kind == MD_KIND_NH ? KICK_NH : (p.kind == MD_KIND_NH_EXACT ? KICK_NH_EXACT : KICK_VV);
   int64_t done = 0;
   bool now_drifted = drifted != 0;
+  // NVE steps that only write a log record keep their partial sums in a slot
+  // of p.plog (slot k: step and record index in p.plog_rec[k]); their records
+  // are formed after the launch by k_log_records, so that no CTA starts the
+  // next step late
+  int ndef = 0;
+
 
   // record where this launch left the state: the gather-buffer parity, the
   // global step, whether positions are one drift ahead of velocities/forces,
@@ -1769,6 +1791,7 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
       C->steps_done = done;
       C->drifted = is_drifted ? 1 : 0;
       C->forces_valid = forces_valid;
+      C->log_slots_used = ndef;
     }
   };
 
@@ -1848,18 +1871,25 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
     const bool last = s == p.nsteps - 1;
     const bool rs = p.kind == MD_KIND_RESAMPLE && (step % p.nstep_boltz == 0);
     const bool fuse = !nh && !rs && !last;
-    double* part = p.part[step & 1];
+    double* part = p.part[step & 1];  // (replaced by a log slot below when deferred)
     const int64_t li = p.log_step0 + s + 1;
     const bool log_now = p.log_every > 0 && (li % p.log_every) == 0 && (li / p.log_every - 1) < p.log_cap;
     const int64_t lidx = p.log_every > 0 ? li / p.log_every - 1 : 0;
     const bool energy = log_now || last;
     const bool need_red = log_now || nh || last || rs;
+    const bool defer = log_now && !nh && !rs && !last && ndef < p.plog_slots;
+    if (defer) part = p.plog + (int64_t)ndef * p.plog_stride;
     force_phase<MIX>(p, sh, cur, kick, fuse, part, true, energy, need_red, step + 1);
     if ((fl = grid_sync(p, sh, 10)) < 0) return;
     if (fuse) cur ^= 1;
     now_drifted = fuse;
-    if (need_red && !reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx))
+    if (defer) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) p.plog_rec[ndef] = make_longlong2(step, lidx);
+      ++ndef;
+    } else if (need_red &&
+               !reduce_phase<MIX>(p, sh, part, p.T, energy ? RED_STEP : RED_STEP_KE, step, log_now && !rs, lidx)) {
       return;
+    }
     if (nh) {
       if ((fl = grid_sync(p, sh, 11)) < 0) return;
       if (!last) {
@@ -1887,6 +1917,28 @@ __global__ void __launch_bounds__(512, KAMD_MIN_BLOCKS) md_persistent(KParams p)
 // Barrier self-test: block 0 leaves without arriving, so the other blocks'
 // wait runs out after timeout_ns and they raise MD_FLAG_TIMEOUT. Nothing is
 // read or written but the control block.
+// The log records of the NVE steps whose partial sums a launch of
+// md_persistent left in slots of p.plog (slot k: step and record index in
+// p.plog_rec[k]; nslots used): one (slot, replica) pair per CTA, the same sums
+// as reduce_phase forms at a step for a replica reduced by one CTA, so the
+// records are those that step would have written. Launched after the
+// persistent kernel on the same stream.
+template <bool MIX>
+__global__ void __launch_bounds__(512) k_log_records(KParams p, int nslots) {
+  __shared__ Shared sh;
+  for (int64_t w = blockIdx.x; w < (int64_t)nslots * p.nrep; w += gridDim.x) {
+    const int k = (int)(w / p.nrep), r = (int)(w - (int64_t)k * p.nrep);
+    RepDev& R = p.reps[r];
+    double acc[6];
+    sum_records<MIX>(sh, p.plog + (int64_t)k * p.plog_stride, (int64_t)R.tile0 * p.T, (int64_t)R.ntiles * p.T, acc);
+    if (threadIdx.x == 0) {
+      const longlong2 rec = p.plog_rec[k];
+      reduce_scalars(p, R, r, acc, RED_LOG, rec.x, true, rec.y, false);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_barrier_selftest(KParams p) {
   __shared__ Shared sh;
   if (blockIdx.x == 0) return;
@@ -1895,6 +1947,16 @@ __global__ void k_barrier_selftest(KParams p) {
 }
 
 }  // namespace kamd
+
+cudaError_t md_launch_log_records(bool mixed, const KParams& p, int nslots, int block, cudaStream_t s) {
+  // the persistent kernel's block size: sum_records strides by it, so the
+  // sums come out in the order the step itself would have used
+  const int64_t pairs = (int64_t)nslots * p.nrep;
+  const int blocks = (int)(pairs < 1024 ? pairs : 1024);
+  if (mixed) kamd::k_log_records<true><<<blocks, block, 0, s>>>(p, nslots);
+  else kamd::k_log_records<false><<<blocks, block, 0, s>>>(p, nslots);
+  return cudaGetLastError();
+}
 
 cudaError_t md_launch_barrier_selftest(const KParams& p, int blocks, cudaStream_t s) {
   kamd::k_barrier_selftest<<<blocks, 32, 0, s>>>(p);

@@ -742,6 +742,27 @@ def test_time_forces_leaves_the_trajectory_unchanged(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,log_every", [(4000, 10), (4000, 1), (1000, 7)])
+def test_log_records_reduced_after_the_launch_equal_those_at_the_step(prec, n, log_every, monkeypatch):
+    """NVE log records whose sums are formed after the launch's last step (the default) are bitwise
+    those formed at their steps (KAMD_LOG_NOW=1), and the trajectory is the same; log_every = 1 has
+    more log steps than the 64 slots of a launch, so both kinds of record occur in one call."""
+    pos, vel, types, L = melted(n, 96, nsteps=100)
+    runs = []
+    for now in ("1", "0"):
+        monkeypatch.setenv("KAMD_LOG_NOW", now)
+        with make_system(n, L, types, prec) as s:
+            s.set_state(pos, vel)
+            log = s.step_nve(0.005, 150, log_every=log_every)
+            runs.append((log, s.get_state()))
+    (la, a), (lb, b) = runs
+    assert len(la) == 150 // log_every and np.all(np.diff(la["step"][:, 0]) == log_every)
+    assert np.array_equal(la, lb)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_time_lists_leaves_a_rebuilt_state(prec):
     """md_time_lists (the list build alone, repeated inside one launch after a full rebuild)
     reports a positive time and leaves the state of a rebuild at unchanged positions: the forces
