@@ -275,11 +275,14 @@ def analysis_cost(torch, s, reps=3):
 
 
 def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY, step=None):
-    """Time `steps` calls of `step(CHUNK, log_every)` (default: NVE) with CUDA events, L2 flushed between."""
+    """Time `steps` calls of `step(CHUNK, log_every)` (default: NVE) with CUDA events, L2 flushed between.
+    Returns (seconds per call, the thermo log, the library's kernel launches during the timed calls)."""
     step = step or (lambda k, le: s.step_nve(dt, k, log_every=le))
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         step(CHUNK, 0)
+    torch.cuda.synchronize()
+    k0 = s.info()["kernel_launches"]  # outside the timed region
     logs, times = [], []
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -291,7 +294,7 @@ def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY, step=N
     torch.cuda.synchronize()
     times = [ev0[k].elapsed_time(ev1[k]) * 1e-3 for k in range(steps)]
     log = np.concatenate(logs, axis=0)
-    return np.array(times), log
+    return np.array(times), log, s.info()["kernel_launches"] - k0
 
 
 def run_e2e(torch, kamd, s, dt, steps, T=None):
@@ -507,7 +510,7 @@ def main():
     rebuilds0 = s.info()["rebuilds"]
     clocks = Clocks(dev)
     clocks.start()
-    times, log = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush, step=stepper(s, T))
+    times, log, launches = timed_chunks(torch, s, wl.DT, args.steps, args.warmup, flush, step=stepper(s, T))
     clk = clocks.stop()
     total = max_over_ranks(float(times.sum()), dist, "cuda")
     n_job = int(round(sum_over_ranks(n_sys, dist))) if dist else n_sys
@@ -561,7 +564,7 @@ def main():
         s64, _, T64 = setup_system(kamd, wl, "fp64", dev, wk, subset=subset)
         if not args.no_autotune:
             s64.autotune(wl.DT, probe_steps=50 if n_sys < 200000 else 10, skin=wk.get("skin"))
-        t64, log64 = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
+        t64, log64, _ = timed_chunks(torch, s64, wl.DT, k64, 1, flush, step=stepper(s64, T64))
         d64 = drift_stats(log64, wl.DT) if wk["timed"] == "nve" else None
         fp64 = {"value": n_sys * CHUNK * k64 / float(t64.sum()), "unit": UNIT, "timed_md_steps": CHUNK * k64,
                 "drift_per_particle_per_tau": d64["slope"] if d64 else None,
@@ -617,7 +620,7 @@ def main():
         "device_bytes": device_bytes,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": int(round(sum_over_ranks(launches, dist))) if dist else int(launches),
         "clocks": clk,
     }
     print(json.dumps(line))

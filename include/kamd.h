@@ -99,6 +99,9 @@ typedef struct {
     int32_t precision;
     int64_t graph_launches;   /* persistent launches issued as CUDA-graph launches */
     int64_t prunes;           /* inner-list prune passes */
+    int64_t kernel_launches;  /* kernels launched by the persistent-kernel operations: each
+                                 launch of the persistent kernel, and of the kernel that forms
+                                 the log records of a launch afterwards */
 } md_info;
 
 /*

@@ -115,6 +115,7 @@ struct md_system {
   int g_grid = 0, g_block = 0;
   size_t g_smem = 0;
   int64_t graph_launches = 0;
+  int64_t kernel_launches = 0;  // persistent launches and log-record launches
   std::string err;
 };
 
@@ -959,12 +960,15 @@ md_status run_op(md_system* s, int op, int kind, double dt, int64_t nsteps, int6
     p.log_cap = log_cap;
     p.thermo = s->d_thermo;
     CK(launch_persistent(s, p));
+    ++s->kernel_launches;
     CKS(download_ctl(s));
     if (op == MD_OP_STEPS) done += s->ctl.steps_done;
     const int pend = s->ctl.pending;
     // log records whose sums the launch left in slots (before a relaunch reuses them)
-    if (!(pend & MD_FLAG_TIMEOUT) && s->ctl.log_slots_used > 0)
+    if (!(pend & MD_FLAG_TIMEOUT) && s->ctl.log_slots_used > 0) {
       CK(md_launch_log_records(s->mixed, p, s->ctl.log_slots_used, s->tun.block_size, s->stream));
+      ++s->kernel_launches;
+    }
     if (pend & MD_FLAG_TIMEOUT) {
       s->have_state = false;
       char buf[160];
@@ -1718,6 +1722,7 @@ md_status md_get_info(md_system* s, md_info* info) {
   info->precision = s->mixed ? MD_PREC_MIXED : MD_PREC_FP64;
   info->graph_launches = s->graph_launches;
   info->prunes = s->ctl.prunes;
+  info->kernel_launches = s->kernel_launches;
   return MD_OK;
 }
 

@@ -48,7 +48,8 @@ class md_info(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
                 ("list_capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("all_pairs_replicas", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("graph_launches", ctypes.c_int64), ("prunes", ctypes.c_int64)]
+                ("graph_launches", ctypes.c_int64), ("prunes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class KamdError(RuntimeError):
