@@ -762,6 +762,22 @@ def test_log_records_reduced_after_the_launch_equal_those_at_the_step(prec, n, l
         assert np.array_equal(x, y)
 
 
+def test_log_records_after_the_launch_with_the_stochastic_bath(monkeypatch):
+    """The stochastic bath (Maxwell-Boltzmann redraw every 50 steps): records of redraw steps are
+    formed at their steps, those of the NVE steps between after the launch; the log is bitwise the
+    one with every record formed at its step (KAMD_LOG_NOW=1)."""
+    pos, vel, types, L = melted(2000, 97, nsteps=100)
+    logs = []
+    for now in ("1", "0"):
+        monkeypatch.setenv("KAMD_LOG_NOW", now)
+        with make_system(2000, L, types, "mixed") as s:
+            s.set_state(pos, vel)
+            logs.append(s.step_nvt(0.005, 150, 1.2, kind=kamd.MD_NVT_RESAMPLE, param=50, seed=7, log_every=10))
+    a, b = logs
+    assert len(a) == 15 and np.all(np.isfinite(a["T"]))
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_time_lists_leaves_a_rebuilt_state(prec):
     """md_time_lists (the list build alone, repeated inside one launch after a full rebuild)
