@@ -762,6 +762,30 @@ def test_log_records_reduced_after_the_launch_equal_those_at_the_step(prec, n, l
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("ntypes", [3, 4])
+def test_forces_with_three_and_four_species(prec, ntypes):
+    """More than two species (the list build's general radius selection, the type tables): a melted
+    N = 4000 liquid relabelled at random into 3 or 4 species with their own symmetric eps/sigma
+    (Lorentz-like mixing, r_c = 2.5 sigma_ab), one and four lanes per particle, against the oracle."""
+    pos, vel, _, L = melted(4000, 23, nsteps=200)
+    rng = np.random.default_rng(40 + ntypes)
+    types = rng.integers(0, ntypes, size=len(pos)).astype(np.int32)
+    sig1 = np.array([1.0, 0.88, 0.94, 0.82])[:ntypes]
+    eps1 = np.array([1.0, 0.5, 0.8, 1.2])[:ntypes]
+    sig = 0.5 * (sig1[:, None] + sig1[None, :])
+    eps = np.sqrt(eps1[:, None] * eps1[None, :])
+    rc = 2.5 * sig
+    f_ref, v_ref, _ = oracle.forces(pos, types, oracle.Params(eps, sig, rc, 1.0), L)
+    for tpa in (1, 4):
+        with kamd.System(len(pos), L, types, eps, sig, rc, 1.0, 0.3, prec) as s:
+            s.set_tuning(threads_per_atom=tpa)
+            s.set_state(pos, vel)
+            f, pe, _ = s.forces()
+        check_forces(f, f_ref, prec)
+        assert abs(pe[0] - v_ref) <= TOL_E[prec] * abs(v_ref)
+
+
 def test_log_records_after_the_launch_with_the_stochastic_bath(monkeypatch):
     """The stochastic bath (Maxwell-Boltzmann redraw every 50 steps): records of redraw steps are
     formed at their steps, those of the NVE steps between after the launch; the log is bitwise the
