@@ -298,13 +298,21 @@ def timed_chunks(torch, s, dt, steps, warmup, flush, log_every=LOG_EVERY, step=N
 
 
 def run_e2e(torch, kamd, s, dt, steps, T=None):
-    """Public API with host buffers: set_state(host) + step (log to host) + get_state(host)."""
-    pos, vel, _ = s.get_state()
-    pos = np.ascontiguousarray(pos)
-    vel = np.ascontiguousarray(vel)
-    img = np.zeros((s.n_total, 3), dtype=np.int32)
+    """Public API with host buffers: set_state(host) + step (log to host) + get_state(host). The host
+    buffers are pinned (page-locked) memory, as a caller streaming states would allocate them."""
+    pos0, vel0, _ = s.get_state()
+    n3 = (s.n_total, 3)
+
+    def pinned(shape, dtype, init=None):
+        t = torch.empty(int(np.prod(shape)) * np.dtype(dtype).itemsize, dtype=torch.uint8, pin_memory=True)
+        a = t.numpy().view(dtype).reshape(shape)
+        a[...] = 0 if init is None else init
+        return a, t  # keep the tensor alive with the view
+
+    (pos, tp), (vel, tv) = pinned(n3, np.float64, pos0), pinned(n3, np.float64, vel0)
+    img, ti = pinned(n3, np.int32)
     nlog = CHUNK // LOG_EVERY
-    log = np.zeros(nlog * s.nrep, dtype=kamd.THERMO_DTYPE)
+    log, tl = pinned((nlog * s.nrep,), kamd.THERMO_DTYPE)
     h = s.handle
     torch.cuda.synchronize()
     t0 = time.perf_counter()
