@@ -340,6 +340,32 @@ def test_batch_replicas_equal_standalone_runs(prec, red_tiles, monkeypatch):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_batch_nve_log_records_and_time_lists(prec):
+    """NVE on a batch: the log records formed after the launch, one (slot, replica) pair per CTA,
+    equal every replica's stand-alone records bitwise; md_time_lists then rebuilds every replica,
+    and each replica's forces are the oracle's at its positions."""
+    ns = [500, 2000, 1000]
+    cfg = [melted(n, 70 + k, nsteps=50) for k, n in enumerate(ns)]
+    Ls = [c[3] for c in cfg]
+    types = np.concatenate([c[2] for c in cfg])
+    with kamd.System(ns, Ls, types, wl.KA_EPS, wl.KA_SIG, wl.KA_RC, 1.0, 0.3, prec) as b:
+        b.set_state(np.concatenate([c[0] for c in cfg]), np.concatenate([c[1] for c in cfg]))
+        blog = b.step_nve(0.005, 120, log_every=10)
+        assert 0.0 < b.time_lists(5) < 1e-2
+        bp, _, _ = b.get_state()
+        bf, _, _ = b.forces()
+    off = 0
+    for k, n in enumerate(ns):
+        with make_system(n, Ls[k], cfg[k][2], prec) as s:
+            s.set_state(cfg[k][0], cfg[k][1])
+            log = s.step_nve(0.005, 120, log_every=10)
+        assert np.array_equal(log[:, 0], blog[:, k])
+        f_ref, _, _ = oracle.forces(bp[off:off + n], cfg[k][2], ka_params(), Ls[k])
+        check_forces(bf[off:off + n], f_ref, prec)
+        off += n
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("skins", [None, (0.3, 0.3), (0.2, 0.5)], ids=["default", "one-list", "dual-0.2-0.5"])
 def test_rebuilds_keep_parity_over_long_nve(prec, skins):
     """400 NVE steps at T=2 cross many list rebuilds (and inner-list prunes, for two lists).
